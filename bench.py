@@ -1,0 +1,530 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 cuckoo-table hot path (arXiv:1605.05236).
+
+One step = fill a 2^24-bin x 4-slot table (2^26 slots, 512 MiB of slots)
+from empty to load 0.95 (63,753,420 keys) in 2^20-key insert batches with
+queue-kicking, then 2^26 lookups at 50% hit, then 2^22 deletes of present
+keys; everything through the C ABI (libck.so) on device-resident inputs.
+The table (512 MiB) and key arrays are larger than L2, so no flush is needed
+between steps.
+
+Prints one JSON line (rank 0).  `value` is M inserts/s over the fills;
+lookups/s, deletes/s, bins viewed per insertion, per-policy fills, the
+roofline of the dominant kernel, the end-to-end number through host buffers
+and the oracle's CPU baseline ride along.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BINS, B = 1 << 24, 4
+LOAD = 0.95
+BATCH = 1 << 20
+N_LOOKUP = 1 << 26
+N_DELETE = 1 << 22
+METRIC = "M inserts/s to load 0.95 & bins viewed/insert; M lookups/s; % of HBM roofline"
+WORKLOAD = ("2-choice cuckoo, 2^24 bins x 4 slots (2^26 slots, 512 MiB), fill from empty to load 0.95 "
+            "(63,753,420 keys) in 2^20-key batches with queue-kicking + claim flags, then 2^26 lookups "
+            "(50% hit) and 2^22 deletes of present keys")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-policies", action="store_true", help="skip the per-policy fills")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def inputs_values(keys):
+    from paper_1605_05236_gb300 import inputs
+    return inputs.values_for(keys)
+
+
+def workload(seed: int):
+    from paper_1605_05236_gb300 import inputs
+    n = inputs.load_target(BINS * B, LOAD)
+    keys, nxt = inputs.distinct_keys(n, seed)
+    vals = inputs.values_for(keys)
+    lk, expect = inputs.lookup_keys(keys, N_LOOKUP, seed, 0.5, next_start=nxt)
+    dk = inputs.delete_keys(keys, N_DELETE, seed)
+    return keys, vals, lk, expect, dk
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % gpu_index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def gather_roofline(torch, ck, nbytes, width, n_reads, stream):
+    """Measured random-gather bandwidth (GB/s) for `width`-byte records over
+    a buffer of `nbytes` (the table's access pattern; bytes counted = reads x width)."""
+    buf = torch.empty(nbytes // 8, dtype=torch.int64, device="cuda")
+    buf.fill_(1)
+    sink = torch.zeros(1024, dtype=torch.int64, device="cuda")
+    for i in range(3):
+        ck.gather_probe(buf, width, n_reads, 17 + i, sink, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = None
+    for i in range(5):
+        e0.record(stream)
+        ck.gather_probe(buf, width, n_reads, 100 + i, sink, stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del buf
+    return n_reads * width / (best * 1e-3) / 1e9
+
+
+def fill_once(torch, ck, table, kt, vt, st, stream, batch=BATCH):
+    """Fill from empty in `batch`-key calls; returns (ms, per-launch ms list)."""
+    n = kt.numel()
+    evs = []
+    table.clear(stream)
+    start = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for lo in range(0, n, batch):
+        hi = min(n, lo + batch)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        table.insert_batch(kt[lo:hi], vt[lo:hi], st[lo:hi], stream)
+        b.record(stream)
+        evs.append((a, b))
+    end = torch.cuda.Event(enable_timing=True)
+    end.record(stream)
+    end.synchronize()
+    return start.elapsed_time(end), [a.elapsed_time(b) for a, b in evs]
+
+
+def batch_profile(torch, ck, table, kt, vt, st, stream):
+    """Diagnostics (outside the timed region): one fill with launches
+    serialised and an event pair around each, to show how a batch's time
+    grows with the load it starts at (its longest chains)."""
+    table.set_param(ck.PARAM_OVERLAP, 0)
+    ms, per = fill_once(torch, ck, table, kt, vt, st, stream)
+    table.set_param(ck.PARAM_OVERLAP, 1)
+    n = kt.numel()
+    idx = sorted(set([0, len(per) // 4, len(per) // 2, (3 * len(per)) // 4, len(per) - 2, len(per) - 1]))
+    return {"serialised_fill_ms": round(ms, 3),
+            "launch_ms_at_load": {"%.3f" % (min(n, i * BATCH) / (BINS * B)): round(per[i], 4) for i in idx}}
+
+
+def policy_fills(torch, ck, stream, base_keys):
+    """One fill per policy on the same shapes (the policy rows of the path)."""
+    from paper_1605_05236_gb300 import inputs
+    out = {}
+    keys, vals = base_keys
+    kt, vt = ck.as_u32_tensor(keys), ck.as_u32_tensor(vals)
+    st = torch.empty(len(keys), dtype=torch.uint8, device="cuda")
+    for name, pol in (("random", ck.RANDOM), ("bfs", ck.BFS), ("sorted", ck.SORTED), ("queue", ck.QUEUE),
+                      ("random+ghost", ck.RANDOM | ck.GHOST), ("bfs+ghost", ck.BFS | ck.GHOST),
+                      ("sorted+ghost", ck.SORTED | ck.GHOST), ("queue+ghost", ck.QUEUE | ck.GHOST)):
+        t = ck.CuckooTable(BINS, B, 2, pol, seed=1)
+        fill_once(torch, ck, t, kt, vt, st, stream)  # warm
+        ms, _ = fill_once(torch, ck, t, kt, vt, st, stream)
+        s = t.stats()
+        out[name] = {"table": "2^24x4", "load": LOAD, "m_inserts_per_s": round(len(keys) / ms / 1e3, 2),
+                     "bins_viewed_per_insert": round(s["bins_viewed_per_insert"], 4),
+                     "kicks_per_insert": round(s["kicks"] / max(1, s["inserts_ok"]), 4),
+                     "chain_max": s["chain_max"], "failed": s["inserts_failed"], "aborted": s["inserts_aborted"],
+                     "claim_aborts": s["aborts"], "conflict_views": s["conflict_views"]}
+        t.close()
+        del t
+        torch.cuda.empty_cache()
+    del kt, vt, st
+    # 8-slot bins at 0.99 and the d-ary tables of the same slot count
+    for name, bins, b, d, pol, load, cap in (
+            ("queue_b8_0.99", 1 << 23, 8, 2, ck.QUEUE, 0.99, 500),
+            ("random_b8_0.99", 1 << 23, 8, 2, ck.RANDOM, 0.99, 500),
+            ("random_d3_0.90", 1 << 26, 1, 3, ck.RANDOM, 0.90, 4096),
+            ("rattle_d3_0.90", 1 << 26, 1, 3, ck.RATTLE, 0.90, 500),
+            ("random_d4_0.96", 1 << 26, 1, 4, ck.RANDOM, 0.96, 4096),
+            ("rattle_d4_0.96", 1 << 26, 1, 4, ck.RATTLE, 0.96, 500)):
+        n = inputs.load_target(bins * b, load)
+        keys, nxt = inputs.distinct_keys(n, 2)
+        kt, vt = ck.as_u32_tensor(keys), ck.as_u32_tensor(inputs.values_for(keys))
+        st = torch.empty(n, dtype=torch.uint8, device="cuda")
+        t = ck.CuckooTable(bins, b, d, pol, seed=1)
+        t.set_param(ck.PARAM_CHAIN_CAP, cap)
+        ms, _ = fill_once(torch, ck, t, kt, vt, st, stream)
+        s = t.stats()
+        rec = {"table": "2^%dx%d d=%d" % (int(np.log2(bins)), b, d), "load": load, "cap": cap,
+               "m_inserts_per_s": round(n / ms / 1e3, 2),
+               "bins_viewed_per_insert": round(s["bins_viewed_per_insert"], 4),
+               "chain_max": s["chain_max"], "failed": s["inserts_failed"], "aborted": s["inserts_aborted"]}
+        if d > 2:
+            lk, expect = inputs.lookup_keys(keys, N_LOOKUP, 2, 0.5, next_start=nxt)
+            lkt = ck.as_u32_tensor(lk)
+            v = torch.empty(N_LOOKUP, dtype=torch.int32, device="cuda")
+            f = torch.empty(N_LOOKUP, dtype=torch.uint8, device="cuda")
+            t.lookup(lkt, v, f, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            t.lookup(lkt, v, f, stream)
+            e1.record(stream)
+            e1.synchronize()
+            rec["m_lookups_per_s"] = round(N_LOOKUP / e0.elapsed_time(e1) / 1e3, 1)
+            rec["lookups_exact"] = bool(torch.equal(f.cpu(), torch.from_numpy(expect)))
+            del lkt, v, f
+        out[name] = rec
+        t.close()
+        del t, kt, vt, st
+        torch.cuda.empty_cache()
+    return out
+
+
+def cpu_baseline():
+    """The oracle, as it stands, on one host core: a bounded sample of the
+    workload (a 2^22-bin x 4-slot table filled to 0.95 with queue-kicking)."""
+    import oracle
+    from paper_1605_05236_gb300 import inputs
+    bins = 1 << 22
+    n = inputs.load_target(bins * B, LOAD)
+    keys, _ = inputs.distinct_keys(n, 1)
+    vals = inputs.values_for(keys)
+    t = oracle.OracleTable(bins, B, 2, oracle.QUEUE, rng_seed=1, cap=500)
+    t0 = time.perf_counter()
+    t.insert(keys, vals)
+    dt = time.perf_counter() - t0
+    s = t.stats()
+    return {"value": round(n / dt / 1e6, 3), "unit": "M inserts/s", "cores": 1, "kind": "oracle",
+            "sample": "serial C oracle, queue-kicking fill of a 2^22-bin x 4-slot table from empty to 0.95 "
+                      "(%d keys, %.1f s); bins viewed/insert %.4f" % (n, dt, s["bins_viewed"] / n)}
+
+
+def run_gpu(args, rank, world, local):
+    import torch
+    from paper_1605_05236_gb300 import ck
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    ck.load()
+    stream = torch.cuda.current_stream()
+    seed = 1 + 1000 * rank  # each rank fills its own table: independent shards (weak scaling)
+    keys, vals, lk, expect, dk = workload(seed)
+    n = len(keys)
+    kt, vt = ck.as_u32_tensor(keys), ck.as_u32_tensor(vals)
+    lkt, dkt = ck.as_u32_tensor(lk), ck.as_u32_tensor(dk)
+    st = torch.empty(n, dtype=torch.uint8, device="cuda")
+    lv = torch.empty(N_LOOKUP, dtype=torch.int32, device="cuda")
+    lf = torch.empty(N_LOOKUP, dtype=torch.uint8, device="cuda")
+    df = torch.empty(N_DELETE, dtype=torch.uint8, device="cuda")
+    table = ck.CuckooTable(BINS, B, 2, ck.QUEUE, seed=seed)
+    n_batches = (n + BATCH - 1) // BATCH
+    launches_per_step = n_batches + 2
+
+    def step(rec):
+        # no events between the insert launches: consecutive launches overlap
+        table.clear(stream)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ins = []
+        e[0].record(stream)
+        for lo in range(0, n, BATCH):
+            hi = min(n, lo + BATCH)
+            table.insert_batch(kt[lo:hi], vt[lo:hi], st[lo:hi], stream)
+        e[1].record(stream)
+        table.lookup(lkt, lv, lf, stream)
+        e[2].record(stream)
+        table.delete(dkt, df, stream)
+        e[3].record(stream)
+        return e, ins
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_begin = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_begin.record(stream)
+    recs = [step(True) for _ in range(args.steps)]
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = t_begin.elapsed_time(t_end)
+    fill_ms = sum(e[0].elapsed_time(e[1]) for e, _ in recs)
+    look_ms = sum(e[1].elapsed_time(e[2]) for e, _ in recs)
+    del_ms = sum(e[2].elapsed_time(e[3]) for e, _ in recs)
+    s = table.stats()  # counters of the last step (ck_clear zeroes them)
+
+    # correctness of the last step (outside the timed region)
+    ok = bool((st == 0).all().item())
+    lookups_exact = bool(torch.equal(lf.cpu(), torch.from_numpy(expect)))
+    present = torch.from_numpy(expect.astype(bool))
+    want = torch.from_numpy(inputs_values(lk).view(np.int32))
+    vals_exact = bool(torch.equal(lv.cpu()[present], want[present]))
+    deletes_exact = bool((df == 1).all().item())
+
+    times = torch.tensor([total_ms, fill_ms, look_ms, del_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(times, op=torch.distributed.ReduceOp.MAX)
+    total_ms, fill_ms, look_ms, del_ms = [float(x) for x in times.cpu()]
+    K = args.steps
+    value = world * n * K / (fill_ms * 1e-3) / 1e6
+    lookups_mops = world * N_LOOKUP * K / (look_ms * 1e-3) / 1e6
+    deletes_mops = world * N_DELETE * K / (del_ms * 1e-3) / 1e6
+
+    # roofline of the dominant kernel (the insert kernel: it takes most of the step)
+    hbm, peak_kind = measured_peaks()
+    viewed, kicks, ins_ok = s["bins_viewed"], s["kicks"], s["inserts_ok"]
+    # per insertion: each bin viewed = one 32-B slot sector + one 32-B metadata sector;
+    # each written slot (kicks + 1) = one 32-B slot sector write + one 32-B metadata
+    # sector atomic; 8 B of key/value in and 1 B of status out
+    ins_bytes = viewed * 64 + (kicks + ins_ok) * 64 + n * 9
+    bytes_per_launch = ins_bytes / n_batches
+    avg_launch_ms = fill_ms / K / n_batches  # launches overlap: fill time per launch
+    achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
+    look_bytes = N_LOOKUP * (2 * 32 + 4 + 4 + 1)
+    look_gbs = look_bytes / (look_ms / K * 1e-3) / 1e9  # per GPU, per lookup launch
+    g32 = gather_roofline(torch, ck, BINS * B * 8, 32, 1 << 26, stream)
+    profile = batch_profile(torch, ck, table, kt, vt, st, stream)
+    roofline = {"kernel": "k_insert<4,QUEUE> (one launch per 2^20-key batch)", "bound": "hbm",
+                "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+                "traffic": None,
+                "bytes_per_launch": int(bytes_per_launch), "avg_launch_ms": round(avg_launch_ms, 4),
+                "vs_random_gather_32B": {"gbs": round(g32, 1), "frac": round(achieved / g32, 4)}}
+    roof_lookup = {"kernel": "k_lookup2<4>", "bound": "hbm", "achieved": round(look_gbs, 1), "peak": hbm,
+                   "unit": "GB/s", "frac": round(look_gbs / hbm, 4),
+                   "bytes_per_lookup": 73, "vs_random_gather_32B": {"gbs": round(g32, 1),
+                                                                     "frac": round(look_gbs / g32, 4)}}
+
+    # end to end through host buffers (pinned), copies inside the timed region
+    e2e = end_to_end(torch, ck, table, keys, vals, lk, dk, stream, K)
+
+    out = {"metric": METRIC, "value": round(value, 2), "unit": "M inserts/s", "n_gpus": world, "steps": K,
+           "warmup": args.warmup, "ms_per_step": round(total_ms / K, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u32 keys/values in u64 slots (integer)",
+           "data": "synthetic (seeded SplitMix64 uniform distinct uint32 keys)",
+           "config": {"workload": WORKLOAD, "l2": "no flush: table (512 MiB) and key arrays exceed the 129 MB L2",
+                      "parallelism": "dp%d (independent table per GPU)" % world},
+           "bins_viewed_per_insert": round(s["bins_viewed_per_insert"], 4),
+           "kicks_per_insert": round(kicks / max(1, ins_ok), 4),
+           "claim_aborts_per_insert": round(s["aborts_per_insert"], 6),
+           "m_lookups_per_s": round(lookups_mops, 1), "m_deletes_per_s": round(deletes_mops, 1),
+           "ms": {"fill": round(fill_ms / K, 3), "lookup": round(look_ms / K, 3), "delete": round(del_ms / K, 3)},
+           "exact": {"all_inserted": ok, "lookups": lookups_exact, "lookup_values": vals_exact,
+                     "deletes": deletes_exact},
+           "roofline": roofline, "roofline_lookup": roof_lookup, "insert_batches": profile,
+           "e2e": e2e, "gpu_launches": launches_per_step * K, "clocks": clk}
+    del kt, vt, lkt, dkt, st, lv, lf, df
+    table.close()
+    torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and not args.no_policies:
+        out["policies"] = policy_fills(torch, ck, stream, (keys, vals))
+    if rank == 0 and world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
+def end_to_end(torch, ck, table, keys, vals, lk, dk, stream, K):
+    """The same step through the public API from pinned host buffers: each
+    batch's keys/values are copied in, the statuses, lookup results and
+    delete results copied out, all inside the timed region."""
+    n = len(keys)
+    hk = torch.from_numpy(keys.view(np.int32)).pin_memory()
+    hv = torch.from_numpy(vals.view(np.int32)).pin_memory()
+    hl = torch.from_numpy(lk.view(np.int32)).pin_memory()
+    hd = torch.from_numpy(dk.view(np.int32)).pin_memory()
+    hst = torch.empty(n, dtype=torch.uint8).pin_memory()
+    hlv = torch.empty(len(lk), dtype=torch.int32).pin_memory()
+    hlf = torch.empty(len(lk), dtype=torch.uint8).pin_memory()
+    hdf = torch.empty(len(dk), dtype=torch.uint8).pin_memory()
+    dk_ = torch.empty(BATCH, dtype=torch.int32, device="cuda")
+    dv_ = torch.empty(BATCH, dtype=torch.int32, device="cuda")
+    ds_ = torch.empty(BATCH, dtype=torch.uint8, device="cuda")
+    dl = torch.empty(len(lk), dtype=torch.int32, device="cuda")
+    dlv = torch.empty(len(lk), dtype=torch.int32, device="cuda")
+    dlf = torch.empty(len(lk), dtype=torch.uint8, device="cuda")
+    ddk = torch.empty(len(dk), dtype=torch.int32, device="cuda")
+    ddf = torch.empty(len(dk), dtype=torch.uint8, device="cuda")
+
+    def step():
+        table.clear(stream)
+        for lo in range(0, n, BATCH):
+            hi = min(n, lo + BATCH)
+            m = hi - lo
+            dk_[:m].copy_(hk[lo:hi], non_blocking=True)
+            dv_[:m].copy_(hv[lo:hi], non_blocking=True)
+            table.insert_batch(dk_[:m], dv_[:m], ds_[:m], stream)
+            hst[lo:hi].copy_(ds_[:m], non_blocking=True)
+        dl.copy_(hl, non_blocking=True)
+        table.lookup(dl, dlv, dlf, stream)
+        hlv.copy_(dlv, non_blocking=True)
+        hlf.copy_(dlf, non_blocking=True)
+        ddk.copy_(hd, non_blocking=True)
+        table.delete(ddk, ddf, stream)
+        hdf.copy_(ddf, non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        step()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    ok = bool((hst == 0).all().item()) and bool((hdf == 1).all().item())
+    h2d = n * 8 + len(lk) * 4 + len(dk) * 4
+    d2h = n * 1 + len(lk) * 5 + len(dk) * 1
+    return {"value": round(n / (ms * 1e-3) / 1e6, 2), "unit": "M inserts/s (whole step incl. copies)",
+            "ms_per_step": round(ms, 3), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "results_exact": ok}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle, as it stands, on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle
+    from paper_1605_05236_gb300 import inputs
+    bins = 1 << 20  # bounded sample: a 2^20-bin x 4-slot table, same load trajectory
+    n = inputs.load_target(bins * B, LOAD)
+    keys, nxt = inputs.distinct_keys(n, 1)
+    vals = inputs.values_for(keys)
+    lk, _ = inputs.lookup_keys(keys, 1 << 22, 1, 0.5, next_start=nxt)
+    dk = inputs.delete_keys(keys, 1 << 18, 1)
+
+    def step():
+        t = oracle.OracleTable(bins, B, 2, oracle.QUEUE, rng_seed=1, cap=500)
+        t0 = time.perf_counter()
+        t.insert(keys, vals)
+        t1 = time.perf_counter()
+        t.lookup(lk)
+        t.delete(dk)
+        t2 = time.perf_counter()
+        return t1 - t0, t2 - t0
+
+    for _ in range(args.warmup):
+        step()
+    fills, totals = [], []
+    for _ in range(args.steps):
+        f, tot = step()
+        fills.append(f)
+        totals.append(tot)
+    value = n * len(fills) / sum(fills) / 1e6
+    sample = ("serial C oracle: queue-kicking fill of a 2^20-bin x 4-slot table to 0.95 (%d keys), "
+              "then 2^22 lookups and 2^18 deletes, per step" % n)
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "M inserts/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(totals) / len(totals), 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32 keys/values in u64 slots (integer)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": round(value, 3), "unit": "M inserts/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 3), "unit": "M inserts/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_gpu(args, rank, world, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

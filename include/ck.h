@@ -1,0 +1,191 @@
+/*
+ * ck.h -- C ABI of libck.so, GB300 (sm_103a) cuckoo hash tables with the
+ * kick-out eviction policies and claim flags of W. Kuszmaul, "Fast
+ * Concurrent Cuckoo Kick-out Eviction Schemes for High-Density Tables"
+ * (arXiv:1605.05236).
+ *
+ * Problem statement (Sec. 1): each key maps to distinct bins by hash
+ * functions; an insertion places the key into a free slot of one of its
+ * bins, otherwise it kicks a resident record out and re-inserts it,
+ * forming a kick-out chain.  Reads, overwrites and deletes touch only the
+ * key's own bins.  Tables are either two hash functions over bins of B = 4
+ * or 8 slots (Sec. 1, Sec. 3) or d = 3 or 4 hash functions over single-slot
+ * bins (d-ary cuckoo hashing, Sec. 7).
+ *
+ * Conventions for every call:
+ *   - Return value: CK_OK (0) or a negative CK_E* code; nothing is launched
+ *     when a call returns an error before launching.  ck_strerror() names a
+ *     code.
+ *   - Key/value/status pointers of the *_batch calls are DEVICE pointers
+ *     owned by the caller; they must stay valid until the stream reaches
+ *     the work.  Keys are uint32; 0xFFFFFFFF is reserved (it marks an empty
+ *     slot) and is rejected per key with CK_ST_INVALID.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Batch
+ *     calls are asynchronous on it.  Calls on one table must be ordered by
+ *     the caller (one stream, or events); a table handle is not safe for
+ *     concurrent use from several host threads.
+ *   - Layout in device memory (one buffer per table): slots (n_bins * B
+ *     uint64, key << 32 | value, all-ones when empty), then one uint32
+ *     metadata word per bin, then device counters, then search scratch.
+ */
+#ifndef CK_H
+#define CK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define CK_OK 0
+#define CK_EINVAL (-1)   /* bad argument (sizes, policy/shape mix, null) */
+#define CK_ENOMEM (-2)   /* device or host allocation failed / buffer too small */
+#define CK_ECUDA (-3)    /* a CUDA runtime call failed */
+#define CK_EBUSY (-4)    /* admission refused (serving form) */
+#define CK_ENOTSUP (-5)  /* combination not implemented */
+
+/* ---- per-key status written by ck_insert_batch ---- */
+#define CK_ST_OK 0       /* inserted */
+#define CK_ST_FAILED 1   /* chain cap / search budget reached; key absent, table as before */
+#define CK_ST_ABORTED 2  /* claim conflicts exceeded the retry limit; key absent */
+#define CK_ST_INVALID 3  /* reserved key 0xFFFFFFFF */
+
+/* ---- kick-out policies (Sec. 3-7), ghost insertions OR-able (Sec. 4) ---- */
+#define CK_RANDOM 0      /* random kicking (Sec. 1) */
+#define CK_BFS 1         /* breadth-first search (Sec. 1, Sec. 5) */
+#define CK_SORTED 2      /* sorted search by spawn count (Sec. 5) */
+#define CK_QUEUE 3       /* queue-kicking, hit counters, hit balancing (Sec. 6) */
+#define CK_RATTLE 4      /* rattle-kicking, d-ary only (Sec. 7) */
+#define CK_GHOST 0x100   /* ghost insertions; with RANDOM/BFS/SORTED/QUEUE, two-choice only */
+
+/* ---- runtime parameters for ck_set_param ---- */
+#define CK_PARAM_CHAIN_CAP 1     /* kick-outs (walks), tries (rattle), bins viewed (search); default 500 */
+#define CK_PARAM_MAX_RETRIES 2   /* claim-conflict retries per key; default 64 */
+#define CK_PARAM_RNG_SEED 3      /* seed of the counter-based kick-out draws */
+#define CK_PARAM_HASH_SEED0 10   /* + i for seed_i, i < d (defaults 0x9E3779B9, 0x85EBCA6B, 0xC2B2AE35, 0x27D4EB2F) */
+#define CK_PARAM_BLOCK 20        /* threads per block of the insert kernels */
+#define CK_PARAM_RATTLE_TIE_RESIDENT 30 /* 1: the resident wins rattle ties (debug reading) */
+#define CK_PARAM_ORDERED_WRITES 31      /* 1 (default): release-ordered chain writes, so a
+                                           concurrently read key is never absent (Sec. 8) */
+#define CK_PARAM_OVERLAP 32     /* 1 (default): an insert launch may start while the previous
+                                   one on the stream finishes its longest chains */
+
+/* ---- ck_insert_batch_ex flags ---- */
+#define CK_INS_SERIAL 1  /* one insertion in flight, keys in batch order (debug/parity) */
+
+/* ---- counters returned by ck_stats (device totals since the last reset) ---- */
+typedef struct ck_stats_t {
+  uint64_t inserts_ok;
+  uint64_t inserts_failed;      /* CK_ST_FAILED */
+  uint64_t inserts_aborted;     /* CK_ST_ABORTED */
+  uint64_t bins_viewed;         /* every bin whose slots an insertion examined (Sec. 3 metric) */
+  uint64_t kicks;               /* records displaced by successful insertions */
+  uint64_t chain_max;           /* longest kick-out chain */
+  uint64_t aborts;              /* attempts abandoned on a claim conflict (Sec. 8) */
+  uint64_t ghost_pairs_made;    /* ghost insertions (Sec. 4) */
+  uint64_t dup_evictions;       /* duplicates overwritten */
+  uint64_t size;                /* distinct live keys */
+  uint64_t live_ghosts;         /* live ghost pairs */
+  uint64_t lookups, lookup_hits;
+  uint64_t deletes, delete_hits, delete_aborts;
+  uint64_t conflict_views;      /* bins viewed again after a lost claim race (included in bins_viewed) */
+  uint64_t total_slots;         /* n_bins * B */
+  double load;                  /* size / total_slots */
+  double bins_viewed_per_insert;/* bins_viewed / (inserts_ok + failed + aborted) */
+  double aborts_per_insert;
+} ck_stats_t;
+
+typedef struct ck_table ck_table; /* opaque; owned by the library */
+
+/* Bytes of device memory a table needs (slots, metadata, counters and,
+ * for the search policies, scratch).  0 when the shape is invalid. */
+size_t ck_required_bytes(uint64_t bins, uint32_t slots_per_bin, uint32_t d, uint32_t policy);
+
+/* Create a table whose device memory the library allocates (cudaMalloc on
+ * the current device) and clears.  bins: n_bins >= d, < 2^32; slots_per_bin:
+ * 4 or 8 with d = 2, 1 with d = 3 or 4; policy: CK_* above.  seed: the
+ * kick-out draw seed.  *out receives the handle.  Synchronous. */
+int ck_create(ck_table **out, uint64_t bins, uint32_t slots_per_bin, uint32_t d,
+              uint32_t policy, uint64_t seed);
+
+/* Same, over caller-owned device memory (e.g. a torch tensor): dev_buf must
+ * be 256-byte aligned and at least ck_required_bytes(...) long; it stays
+ * owned by the caller and must outlive the table.  Cleared on `stream`. */
+int ck_create_on(ck_table **out, void *dev_buf, size_t bytes, uint64_t bins,
+                 uint32_t slots_per_bin, uint32_t d, uint32_t policy, uint64_t seed,
+                 void *stream);
+
+/* Set a CK_PARAM_*; CK_EINVAL for an unknown key or out-of-range value. */
+int ck_set_param(ck_table *t, int key, int64_t value);
+
+/* Insert n keys with values (Sec. 1; the paper assumes each key is absent
+ * and distinct, Sec. 3 -- a key already present gets a second copy).
+ * Concurrent insertions claim every slot they will write with a one-bit
+ * claim flag and skip slots others claimed (Sec. 8 "Claim Flags"); chains
+ * are executed back to front (Sec. 8 "System-Transaction Kick-Outs"), so a
+ * failed or aborted insertion changes nothing.  d_status (nullable): n
+ * CK_ST_* bytes. */
+int ck_insert_batch(ck_table *t, const uint32_t *d_keys, const uint32_t *d_vals, uint64_t n,
+                    uint8_t *d_status, void *stream);
+
+/* As ck_insert_batch, plus d_viewed (nullable): bins viewed by each key,
+ * and flags (CK_INS_SERIAL). */
+int ck_insert_batch_ex(ck_table *t, const uint32_t *d_keys, const uint32_t *d_vals, uint64_t n,
+                       uint8_t *d_status, uint32_t *d_viewed, uint32_t flags, void *stream);
+
+/* Look up n keys (Sec. 1: a present key is in one of its bins).  Writes
+ * d_vals_out[i] (0 when absent) and d_found[i] in {0,1}; either nullable. */
+int ck_lookup_batch(ck_table *t, const uint32_t *d_keys, uint64_t n, uint32_t *d_vals_out,
+                    uint8_t *d_found, void *stream);
+
+/* Delete n keys (Sec. 1), every copy of a ghost pair included.  d_found[i]
+ * (nullable) = 1 if this call removed the key.  A slot claimed by an
+ * in-flight insertion is not waited on (Sec. 8): the delete retries a
+ * bounded number of times, then reports 2 in d_found. */
+int ck_delete_batch(ck_table *t, const uint32_t *d_keys, uint64_t n, uint8_t *d_found,
+                    void *stream);
+
+/* Copy the device counters (synchronises the table's last stream). */
+int ck_stats(ck_table *t, ck_stats_t *out);
+
+/* Bins-viewed histogram by load before each insertion, 200 buckets of
+ * 0.5%: views[i], inserts[i] for load in [i/200, (i+1)/200).  Host arrays
+ * of 200 uint64 each; synchronous. */
+int ck_load_histogram(ck_table *t, uint64_t *views, uint64_t *inserts);
+
+/* Zero the counters (asynchronous on the last stream used). */
+int ck_reset_stats(ck_table *t);
+
+/* Empty the table and zero the counters (asynchronous). */
+int ck_clear(ck_table *t, void *stream);
+
+/* Copy the table to host memory (synchronous): slots (n_bins*B uint64) and
+ * meta (n_bins uint32: bits 0-7 claim, 8-15 duplicate, 16-19 spawn count,
+ * 20-27 hit counter, 28-31 version; d-ary: bit 0 claim, 8-15 rattle
+ * counter).  Either pointer may be NULL. */
+int ck_export(ck_table *t, uint64_t *h_slots, uint32_t *h_meta);
+
+/* Free the table (and its memory, when ck_create allocated it). */
+void ck_destroy(ck_table *t);
+
+/* Shape of a table: any pointer may be NULL. */
+int ck_shape(const ck_table *t, uint64_t *bins, uint32_t *slots_per_bin, uint32_t *d,
+             uint32_t *policy);
+
+const char *ck_strerror(int code);
+
+/* Measurement helper (not an operation of the paper): n_reads independent
+ * random reads of `width` bytes (8, 32 or 64: one single-slot, 4-slot or
+ * 8-slot bin) from a device buffer of `bytes` bytes (64-byte aligned), the
+ * access pattern of lookups and insertions.  Timing it gives the measured
+ * random-gather roofline the table kernels are reported against.  d_sink:
+ * 8 KB of device memory the kernel may write.  Asynchronous. */
+int ck_gather_probe(const void *d_buf, size_t bytes, uint32_t width, uint64_t n_reads,
+                    uint64_t seed, void *d_sink, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CK_H */

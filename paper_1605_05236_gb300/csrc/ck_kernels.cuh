@@ -1,0 +1,415 @@
+// ck_kernels.cuh -- the bulk kernels of the GB300 cuckoo table: insert
+// (every policy), lookup and delete (Kuszmaul, arXiv:1605.05236, Sec. 1,
+// Sec. 3-8), plus their per-batch counters.
+#pragma once
+#include "ck_search.cuh"
+
+namespace ck {
+
+// Block-wide accumulation of per-thread counts, then one global add each.
+struct BlockCounters {
+  unsigned long long v[C_N];
+};
+
+__device__ __forceinline__ void flush_counter(unsigned long long* shared_slot, unsigned long long x) {
+  if (x) atomicAdd(shared_slot, x);
+}
+
+__device__ __forceinline__ void backoff(uint32_t attempt, uint32_t key) {
+  uint32_t ns = 64u << (attempt < 6 ? attempt : 6);
+  __nanosleep(ns + (fmix32(key ^ attempt) & 63u));
+}
+
+template <int B, int POL, bool GHOST>
+__device__ __forceinline__ int attempt_insert(const DevTable& t, Ctx& c, uint8_t* region) {
+  if constexpr (B == 1) {
+    return POL == P_RATTLE ? insert_rattle(t, c) : insert_random_dary(t, c);
+  } else if constexpr (POL == P_QUEUE) {
+    return insert_queue<B, GHOST>(t, c);
+  } else if constexpr (POL == P_BFS || POL == P_SORTED) {
+    return insert_search<B, POL == P_SORTED, GHOST>(t, c, region);
+  } else {
+    return insert_random2<B, GHOST>(t, c);
+  }
+}
+
+// Take a free scratch plan (for a chain longer than the local plan holds).
+// Never waits unboundedly: after a bounded number of sweeps it gives up.
+__device__ __forceinline__ int acquire_long(const DevTable& t, uint32_t key) {
+  for (uint32_t round = 0; round < 256; round++) {
+    uint32_t start = fmix32(key + round) % t.n_long;
+    for (uint32_t k = 0; k < t.n_long; k++) {
+      uint32_t r = start + k;
+      if (r >= t.n_long) r -= t.n_long;
+      if (*(volatile uint32_t*)(t.long_busy + r) == 0 && atomicCAS(t.long_busy + r, 0u, 1u) == 0u) return (int)r;
+    }
+    __nanosleep(1000);
+  }
+  return -1;
+}
+
+__device__ __forceinline__ void release_long(const DevTable& t, int r) {
+  __threadfence();
+  atomicExch(t.long_busy + r, 0u);
+}
+
+// One insertion with bounded retries after claim conflicts.  A chain that
+// outgrows the local plan is planned again, with the same draws, in a
+// scratch-backed plan.
+template <int B, int POL, bool GHOST>
+__device__ __forceinline__ int insert_one(const DevTable& t, Ctx& c, uint8_t* region, uint32_t& aborts,
+                                          Plan local) {
+  Plan lp;
+  Plan* plan = &local;
+  int long_id = -1;
+  int st;
+  for (uint32_t attempt = 0;;) {
+    c.attempt = attempt;
+    c.kicks = 0;
+    c.draws = 0;
+    c.viewed0 = c.viewed;
+    c.ghosts_made = 0;
+    c.dup_evict = 0;
+    c.foreign = 0;
+    plan->n = 0;
+    c.plan = plan;
+    st = attempt_insert<B, POL, GHOST>(t, c, region);
+    if (st == ST_OK) {
+      commit<B>(t, c);
+      break;
+    }
+    release_all(t, c);
+    if (st == ST_LONG) {
+      if (long_id >= 0) { st = ST_FAILED; break; }  // a scratch plan holds any chain under the cap
+      long_id = acquire_long(t, c.key);
+      if (long_id < 0) { st = ST_ABORTED; break; }
+      lp = plan_in(t.long_scratch + (uint64_t)long_id * LONG_REGION);
+      plan = &lp;
+      continue;
+    }
+    if (st == ST_FAILED) break;
+    aborts++;
+    if (++attempt >= t.max_retries) { st = ST_ABORTED; break; }
+    backoff(attempt, c.key);
+  }
+  if (long_id >= 0) release_long(t, long_id);
+  return st;
+}
+
+// Insert kernel.  Concurrent mode: a grid-stride loop, one insertion per
+// thread at a time, plans in local memory.  Serial mode (SERIAL, one
+// thread): keys in batch order, one insertion in flight, a scratch-backed
+// plan; this replays the paper's serial algorithms exactly.
+//
+// Consecutive insert launches may overlap (programmatic dependent launch):
+// each block lets the next launch start at once, and each thread waits for
+// the previous launch to finish before it exits, so a launch completes only
+// after its predecessor.  Insertions of distinct absent keys commute under
+// the claim protocol, so the overlap changes no result.  `load_base` is the
+// number of keys the table held before this batch (for the histogram).
+template <int B, int POL, bool GHOST, bool SERIAL>
+__global__ void __launch_bounds__(256) k_insert(DevTable t, const uint32_t* __restrict__ keys,
+                                                const uint32_t* __restrict__ vals, uint64_t n,
+                                                uint8_t* __restrict__ status,
+                                                uint32_t* __restrict__ viewed_out, uint64_t load_base) {
+  asm volatile("griddepcontrol.launch_dependents;");
+  __shared__ unsigned int h_views[HIST_BUCKETS];
+  __shared__ unsigned int h_cnt[HIST_BUCKETS];
+  __shared__ unsigned long long bc[C_N];
+  for (int i = threadIdx.x; i < HIST_BUCKETS; i += blockDim.x) h_views[i] = h_cnt[i] = 0;
+  for (int i = threadIdx.x; i < C_N; i += blockDim.x) bc[i] = 0;
+  __syncthreads();
+
+  PlanStore<SERIAL ? 1 : MAX_CHAIN> store;
+  Plan local = SERIAL ? plan_in(t.long_scratch) : store.view();
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint8_t* region = t.scratch ? t.scratch + tid * SEARCH_REGION : nullptr;
+  const unsigned long long size_base = load_base;
+
+  unsigned long long ok = 0, failed = 0, aborted = 0, viewed = 0, kicks = 0, ghosts = 0, dupev = 0;
+  unsigned long long reviews = 0;
+  uint32_t aborts = 0, chain_max = 0;
+  for (uint64_t i = tid; i < n; i += stride) {
+    uint32_t key = keys[i];
+    if (key == RESERVED_KEY) {
+      if (status) status[i] = ST_INVALID;
+      if (viewed_out) viewed_out[i] = 0;
+      continue;
+    }
+    Ctx c;
+    c.key = key;
+    c.krec = ((uint64_t)key << 32) | vals[i];
+    c.viewed = 0;
+    c.reviews = 0;
+    int st = insert_one<B, POL, GHOST>(t, c, region, aborts, local);
+    if (st == ST_OK) {
+      ok++;
+      kicks += c.kicks;
+      chain_max = max(chain_max, c.kicks);
+      ghosts += c.ghosts_made;
+      dupev += c.dup_evict;
+    } else if (st == ST_FAILED) {
+      failed++;
+    } else {
+      aborted++;
+    }
+    viewed += c.viewed;
+    reviews += c.reviews;
+    if (status) status[i] = (uint8_t)st;
+    if (viewed_out) viewed_out[i] = c.viewed;
+    uint64_t bucket = ((size_base + i) * HIST_BUCKETS) / t.total_slots;
+    if (bucket >= HIST_BUCKETS) bucket = HIST_BUCKETS - 1;
+    atomicAdd(&h_views[bucket], c.viewed);
+    atomicAdd(&h_cnt[bucket], 1u);
+  }
+  flush_counter(&bc[C_INS_OK], ok);
+  flush_counter(&bc[C_INS_FAILED], failed);
+  flush_counter(&bc[C_INS_ABORTED], aborted);
+  flush_counter(&bc[C_VIEWED], viewed);
+  flush_counter(&bc[C_KICKS], kicks);
+  flush_counter(&bc[C_ABORTS], aborts);
+  flush_counter(&bc[C_GHOSTS_MADE], ghosts);
+  flush_counter(&bc[C_DUP_EVICT], dupev);
+  flush_counter(&bc[C_REVIEWS], reviews);
+  if (chain_max) atomicMax(&bc[C_CHAIN_MAX], (unsigned long long)chain_max);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < C_N; k++) {
+      if (!bc[k]) continue;
+      if (k == C_CHAIN_MAX) atomicMax(t.counters + k, bc[k]);
+      else atomicAdd(t.counters + k, bc[k]);
+    }
+    // size and live ghosts follow from the counts above
+    if (bc[C_INS_OK]) atomicAdd(t.counters + C_SIZE, bc[C_INS_OK]);
+    long long dg = (long long)bc[C_GHOSTS_MADE] - (long long)bc[C_DUP_EVICT];
+    if (dg) atomicAdd(t.counters + C_LIVE_GHOSTS, (unsigned long long)dg);
+  }
+  unsigned long long* hist = t.counters + C_N;
+  for (int i = threadIdx.x; i < HIST_BUCKETS; i += blockDim.x) {
+    if (h_cnt[i]) {
+      atomicAdd(hist + i, (unsigned long long)h_views[i]);
+      atomicAdd(hist + HIST_BUCKETS + i, (unsigned long long)h_cnt[i]);
+    }
+  }
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// ------------------------------------------------------------------
+// lookups (Sec. 1: a present key sits in one of its d bins)
+// ------------------------------------------------------------------
+
+// Read-only 32-byte sector load through the non-coherent path: lookups run
+// with no writer in flight on the table.
+__device__ __forceinline__ void ld_bin4_nc(const uint64_t* p, uint64_t* s) {
+  asm volatile("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];"
+               : "=l"(s[0]), "=l"(s[1]), "=l"(s[2]), "=l"(s[3]) : "l"(p));
+}
+
+__device__ __forceinline__ uint64_t ld_slot_nc(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.global.nc.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+
+template <int B>
+__device__ __forceinline__ bool match_bin(const uint64_t* s, uint32_t key, uint32_t& val) {
+  bool f = false;
+#pragma unroll
+  for (int q = 0; q < B; q++) {
+    if (!f && key_of(s[q]) == key) { f = true; val = (uint32_t)s[q]; }
+  }
+  return f;
+}
+
+template <int B>
+__device__ __forceinline__ void load_bin_nc(const DevTable& t, uint32_t bin, uint64_t* s) {
+  const uint64_t* p = t.slots + (uint64_t)bin * B;
+#pragma unroll
+  for (int q = 0; q < B; q += 4) ld_bin4_nc(p + q, s + q);
+}
+
+// Two-choice lookup: both bins are fetched at once (two independent sector
+// loads in flight per key).
+template <int B>
+__global__ void __launch_bounds__(256) k_lookup2(DevTable t, const uint32_t* __restrict__ keys, uint64_t n,
+                                                 uint32_t* __restrict__ vals_out,
+                                                 uint8_t* __restrict__ found_out) {
+  __shared__ unsigned long long hits_sh, cnt_sh;
+  if (threadIdx.x == 0) hits_sh = cnt_sh = 0;
+  __syncthreads();
+  uint32_t hits = 0, cnt = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    uint32_t key = __ldcs(keys + i);
+    uint32_t val = 0;
+    bool f = false;
+    if (key != RESERVED_KEY) {
+      uint32_t b0, b1;
+      bins2(t, key, b0, b1);
+      uint64_t s0[B], s1[B];
+      load_bin_nc<B>(t, b0, s0);
+      load_bin_nc<B>(t, b1, s1);
+      f = match_bin<B>(s0, key, val);
+      if (!f) f = match_bin<B>(s1, key, val);
+    }
+    hits += f;
+    cnt++;
+    if (vals_out) __stcs(vals_out + i, val);
+    if (found_out) __stcs(found_out + i, (uint8_t)f);
+  }
+  hits = __reduce_add_sync(0xffffffffu, hits);
+  cnt = __reduce_add_sync(0xffffffffu, cnt);
+  if ((threadIdx.x & 31) == 0) {
+    if (hits) atomicAdd(&hits_sh, (unsigned long long)hits);
+    if (cnt) atomicAdd(&cnt_sh, (unsigned long long)cnt);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (hits_sh) atomicAdd(t.counters + C_LOOKUP_HITS, hits_sh);
+    if (cnt_sh) atomicAdd(t.counters + C_LOOKUPS, cnt_sh);
+  }
+}
+
+// d-ary lookup: the d single-slot bins are fetched at once.
+__global__ void __launch_bounds__(256) k_lookup_dary(DevTable t, const uint32_t* __restrict__ keys, uint64_t n,
+                                                     uint32_t* __restrict__ vals_out,
+                                                     uint8_t* __restrict__ found_out) {
+  __shared__ unsigned long long hits_sh, cnt_sh;
+  if (threadIdx.x == 0) hits_sh = cnt_sh = 0;
+  __syncthreads();
+  uint32_t hits = 0, cnt = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    uint32_t key = __ldcs(keys + i);
+    uint32_t val = 0;
+    bool f = false;
+    if (key != RESERVED_KEY) {
+      uint32_t b[4];
+      bins_of(t, key, b);
+      uint64_t s[4];
+#pragma unroll
+      for (int j = 0; j < 4; j++) s[j] = j < (int)t.d ? ld_slot_nc(t.slots + b[j]) : EMPTY;
+#pragma unroll
+      for (int j = 0; j < 4; j++)
+        if (!f && key_of(s[j]) == key) { f = true; val = (uint32_t)s[j]; }
+    }
+    hits += f;
+    cnt++;
+    if (vals_out) __stcs(vals_out + i, val);
+    if (found_out) __stcs(found_out + i, (uint8_t)f);
+  }
+  hits = __reduce_add_sync(0xffffffffu, hits);
+  cnt = __reduce_add_sync(0xffffffffu, cnt);
+  if ((threadIdx.x & 31) == 0) {
+    if (hits) atomicAdd(&hits_sh, (unsigned long long)hits);
+    if (cnt) atomicAdd(&cnt_sh, (unsigned long long)cnt);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (hits_sh) atomicAdd(t.counters + C_LOOKUP_HITS, hits_sh);
+    if (cnt_sh) atomicAdd(t.counters + C_LOOKUPS, cnt_sh);
+  }
+}
+
+// ------------------------------------------------------------------
+// deletes (Sec. 1): every copy goes, each under its claim flag (Sec. 8)
+// ------------------------------------------------------------------
+// The copies a delete removes (at most d bins of B slots).
+struct DelPlan {
+  uint32_t bin[16];
+  uint8_t slot[16];
+  uint8_t old_r[16];  // two-choice: duplicate mark; d-ary: rattle counter
+  int n;
+};
+
+template <int B>
+__device__ __forceinline__ int delete_one(const DevTable& t, uint32_t key, DelPlan& p, uint32_t& ghost_removed) {
+  uint32_t b[4];
+  bins_of(t, key, b);
+  const uint32_t nb = t.d;
+  for (int attempt = 0; attempt < 16; attempt++) {
+    p.n = 0;
+    bool conflict = false, any = false;
+    int dup_copies = 0;
+    for (uint32_t j = 0; j < nb && !conflict; j++) {
+      View<B> v;
+      load_view<B>(t, b[j], v);
+      uint32_t m = v.m;
+      uint32_t add = 0;
+      int first = -1;
+#pragma unroll
+      for (int s = 0; s < B; s++) {
+        if (v.s[s] != EMPTY && key_of(v.s[s]) == key) {
+          if ((m >> s) & 1u) { conflict = true; break; }  // an insertion holds it: no waiting
+          add |= 1u << s;
+          if (first < 0) first = s;
+        }
+      }
+      if (conflict || !add) continue;
+      if (!cas_acquire(t.meta + b[j], m, m + add)) { conflict = true; break; }
+      any = true;
+      for (int s = 0; s < B; s++) {
+        if ((add >> s) & 1u) {
+          int i = p.n++;
+          p.bin[i] = b[j];
+          p.slot[i] = (uint8_t)s;
+          p.old_r[i] = (uint8_t)((B == 1) ? rattle_of(m) : ((m >> (DUP_SHIFT + s)) & 1u));
+          dup_copies += (B > 1) ? p.old_r[i] : 0;
+        }
+      }
+    }
+    if (conflict) {
+      for (int i = 0; i < p.n; i++) add_relaxed(t.meta + p.bin[i], 0u - (1u << p.slot[i]));
+      p.n = 0;
+      __nanosleep(128u << (attempt < 5 ? attempt : 5));
+      continue;
+    }
+    if (!any) return 0;
+    for (int i = 0; i < p.n; i++) st_slot(t.slots + (uint64_t)p.bin[i] * B + p.slot[i], EMPTY);
+    for (int i = 0; i < p.n; i++) {
+      uint32_t delta = VER_ONE - (1u << p.slot[i]);
+      if (B == 1) delta -= (uint32_t)p.old_r[i] << RATTLE_SHIFT;        // the bin forgets r(x)
+      else if (p.old_r[i]) delta -= 1u << (DUP_SHIFT + p.slot[i]);       // duplicate mark goes too
+      add_release(t.meta + p.bin[i], delta);
+    }
+    ghost_removed += dup_copies >= 2 ? 1 : 0;
+    return 1;
+  }
+  return 2;
+}
+
+template <int B>
+__global__ void __launch_bounds__(256) k_delete(DevTable t, const uint32_t* __restrict__ keys, uint64_t n,
+                                                uint8_t* __restrict__ found_out) {
+  __shared__ unsigned long long bc[4];
+  if (threadIdx.x < 4) bc[threadIdx.x] = 0;
+  __syncthreads();
+  DelPlan p;
+  uint32_t hits = 0, aborts = 0, ghosts = 0, cnt = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    uint32_t key = keys[i];
+    int r = key == RESERVED_KEY ? 0 : delete_one<B>(t, key, p, ghosts);
+    hits += r == 1;
+    aborts += r == 2;
+    cnt++;
+    if (found_out) found_out[i] = (uint8_t)r;
+  }
+  if (hits) atomicAdd(&bc[0], (unsigned long long)hits);
+  if (aborts) atomicAdd(&bc[1], (unsigned long long)aborts);
+  if (ghosts) atomicAdd(&bc[2], (unsigned long long)ghosts);
+  if (cnt) atomicAdd(&bc[3], (unsigned long long)cnt);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (bc[0]) {
+      atomicAdd(t.counters + C_DELETE_HITS, bc[0]);
+      atomicAdd(t.counters + C_SIZE, 0ull - bc[0]);
+    }
+    if (bc[1]) atomicAdd(t.counters + C_DELETE_ABORTS, bc[1]);
+    if (bc[2]) atomicAdd(t.counters + C_LIVE_GHOSTS, 0ull - bc[2]);
+    if (bc[3]) atomicAdd(t.counters + C_DELETES, bc[3]);
+  }
+}
+
+}  // namespace ck

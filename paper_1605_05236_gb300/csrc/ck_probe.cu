@@ -1,0 +1,77 @@
+// ck_probe.cu -- random-gather microbenchmark: the measured roofline for
+// the table's access pattern (independent random reads of one sector-sized
+// record: 8 B for a single-slot bin, 32 B for a 4-slot bin, 64 B for an
+// 8-slot bin) over a buffer the size of the table.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ck.h"
+
+namespace {
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <int W>  // bytes per record: 8, 32 or 64
+__global__ void __launch_bounds__(256) k_gather(const uint64_t* __restrict__ buf, uint64_t n_records,
+                                                uint64_t mask, uint64_t n_reads, uint64_t seed,
+                                                uint64_t* __restrict__ sink) {
+  constexpr int U = 8;  // independent reads in flight per thread
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t acc = 0;
+  for (uint64_t i = tid * U; i < n_reads; i += stride * U) {  // U consecutive indices per thread
+    uint64_t v[U][W / 8];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      uint64_t h = mix64(seed ^ (i + u));
+      uint64_t r = mask ? (h & mask) : h % n_records;
+      const uint64_t* p = buf + r * (W / 8);
+      if (i + u < n_reads) {
+        if constexpr (W == 8) {
+          asm volatile("ld.global.nc.u64 %0, [%1];" : "=l"(v[u][0]) : "l"(p));
+        } else {
+#pragma unroll
+          for (int q = 0; q < W / 8; q += 4)
+            asm volatile("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];"
+                         : "=l"(v[u][q]), "=l"(v[u][q + 1]), "=l"(v[u][q + 2]), "=l"(v[u][q + 3])
+                         : "l"(p + q));
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < W / 8; q++) v[u][q] = 0;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++)
+#pragma unroll
+      for (int q = 0; q < W / 8; q++) acc ^= v[u][q];
+  }
+  if (acc == 0x0123456789ABCDEFull) sink[tid & 1023] = acc;  // keeps the loads live
+}
+
+}  // namespace
+
+extern "C" int ck_gather_probe(const void* d_buf, size_t bytes, uint32_t width, uint64_t n_reads,
+                               uint64_t seed, void* d_sink, void* stream) {
+  if (!d_buf || !d_sink || (width != 8 && width != 32 && width != 64)) return CK_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(d_buf) % 64) != 0 || bytes < 64) return CK_EINVAL;
+  uint64_t n_records = bytes / width;
+  uint64_t mask = (n_records & (n_records - 1)) == 0 ? n_records - 1 : 0;
+  uint64_t threads = (n_reads + 7) / 8;
+  uint64_t grid = (threads + 255) / 256;
+  if (grid > 152ull * 64) grid = 152ull * 64;  // grid-stride beyond a few waves
+  if (grid == 0) grid = 1;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const uint64_t* b = static_cast<const uint64_t*>(d_buf);
+  uint64_t* k = static_cast<uint64_t*>(d_sink);
+  if (width == 8) k_gather<8><<<(unsigned)grid, 256, 0, s>>>(b, n_records, mask, n_reads, seed, k);
+  else if (width == 32) k_gather<32><<<(unsigned)grid, 256, 0, s>>>(b, n_records, mask, n_reads, seed, k);
+  else k_gather<64><<<(unsigned)grid, 256, 0, s>>>(b, n_records, mask, n_reads, seed, k);
+  return cudaGetLastError() == cudaSuccess ? CK_OK : CK_ECUDA;
+}

@@ -1,0 +1,199 @@
+// ck_search.cuh -- breadth-first search and sorted search for a kick-out
+// chain (Kuszmaul, arXiv:1605.05236, Sec. 5), with ghost insertions (Sec. 4)
+// and claim flags (Sec. 8).
+//
+// Candidates are the records of the bins viewed so far that have not been
+// spawned, kept as groups (one per viewed bin, in viewing order; a group's
+// records pop in slot order).  Spawning a record views its other bin; a
+// free slot there (or, with ghosts, a duplicate) ends the search.  A bin
+// already viewed is never viewed again (the small visited set of Sec. 5,
+// bin index as hash).  BFS pops the oldest candidate; sorted search pops the
+// candidate with the smallest spawn count, oldest first among equals, where
+// a candidate's count is its bin's spawn count when the bin was viewed
+// (the bucket-sort key of Sec. 5).  Spawning a record increments the spawn
+// count of its bin (4 bits, saturating), and the increment stays even if
+// the search fails.
+//
+// The search itself takes no claims.  When it succeeds, every slot of the
+// path is claimed by CAS from the metadata word read when its bin was
+// viewed; a bin that changed since then aborts the attempt.
+//
+// Per-searcher scratch (global memory, SEARCH_REGION bytes): a 16-byte
+// header holding a generation counter, MAX_GROUPS group records, and an
+// open-addressed visited set tagged with the generation (never cleared).
+#pragma once
+#include "ck_insert.cuh"
+
+namespace ck {
+
+struct Group {
+  uint32_t bin;
+  uint32_t meta;    // metadata word as viewed (updated by our own spawn increments)
+  uint32_t parent;  // (group << 3) | slot of the record that led here; ~0u at a root
+  uint8_t next;     // next slot to pop
+  uint8_t skey;     // sort key: spawn count when viewed
+  uint8_t stale;    // the bin changed under us: a path through it aborts
+  uint8_t pad;
+};
+static_assert(sizeof(Group) == 16, "group record is 16 bytes");
+
+constexpr size_t SEARCH_REGION = 16 + MAX_GROUPS * sizeof(Group) + VISITED_SLOTS * 8;
+
+__device__ __forceinline__ uint32_t vis_hash(uint32_t bin) { return (bin * 0x9E3779B1u) >> (32 - 10); }
+
+// Insert `bin` into the visited set; returns false if it was already there.
+__device__ __forceinline__ bool vis_insert(uint64_t* vis, uint32_t gen, uint32_t bin) {
+  uint64_t tag = ((uint64_t)gen << 32) | bin;
+  for (uint32_t h = vis_hash(bin);; h = (h + 1) & (VISITED_SLOTS - 1)) {
+    uint64_t e = vis[h];
+    if (e == tag) return false;
+    if ((uint32_t)(e >> 32) != gen) { vis[h] = tag; return true; }
+  }
+}
+
+__device__ __forceinline__ bool vis_has(const uint64_t* vis, uint32_t gen, uint32_t bin) {
+  uint64_t tag = ((uint64_t)gen << 32) | bin;
+  for (uint32_t h = vis_hash(bin);; h = (h + 1) & (VISITED_SLOTS - 1)) {
+    uint64_t e = vis[h];
+    if (e == tag) return true;
+    if ((uint32_t)(e >> 32) != gen) return false;
+  }
+}
+
+template <int B, bool SORTED, bool GHOST>
+__device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
+  uint32_t b0, b1;
+  bins2(t, c.key, b0, b1);
+  View<B> v0, v1;
+  load_view<B>(t, b0, v0);
+  load_view<B>(t, b1, v1);
+  c.viewed += 2;
+  uint32_t f0 = free_mask<B>(v0), f1 = free_mask<B>(v1);
+  if (GHOST) {
+    if (f0 && f1) {
+      if (!claim(t, c, b0, v0.m, lowest(f0), EMPTY, K_GHOST, false)) return ST_CONFLICT;
+      if (!claim(t, c, b1, v1.m, lowest(f1), EMPTY, K_GHOST, false)) return ST_CONFLICT;
+      c.ghosts_made++;
+      return ST_OK;
+    }
+    if (f0) return take_free<B>(t, c, b0, v0, lowest(f0), false);
+    if (f1) return take_free<B>(t, c, b1, v1, lowest(f1), false);
+    uint32_t d0 = dup_mask<B>(v0), d1 = dup_mask<B>(v1);
+    if (d0) return take_dup<B>(t, c, b0, v0, lowest(d0), false);
+    if (d1) return take_dup<B>(t, c, b1, v1, lowest(d1), false);
+  } else {
+    if (f0) return take_free<B>(t, c, b0, v0, lowest(f0), false);
+    if (f1) return take_free<B>(t, c, b1, v1, lowest(f1), false);
+  }
+
+  uint32_t* hdr = reinterpret_cast<uint32_t*>(region);
+  Group* G = reinterpret_cast<Group*>(region + 16);
+  uint64_t* vis = reinterpret_cast<uint64_t*>(region + 16 + MAX_GROUPS * sizeof(Group));
+  uint32_t gen = hdr[0] + 1;
+  if (gen == 0) gen = 1;
+  hdr[0] = gen;
+
+  uint32_t ng = 0, head = 0;
+  auto push = [&](uint32_t bin, uint32_t m, uint32_t parent) {
+    Group g;
+    g.bin = bin;
+    g.meta = m;
+    g.parent = parent;
+    g.next = 0;
+    g.skey = (uint8_t)spawn_of(m);
+    g.stale = 0;
+    g.pad = 0;
+    G[ng++] = g;
+    vis_insert(vis, gen, bin);
+  };
+  push(b0, v0.m, ~0u);
+  push(b1, v1.m, ~0u);
+
+  for (;;) {
+    // pick the group to pop from
+    while (head < ng && G[head].next >= B) head++;
+    if (head == ng) return c.foreign ? ST_CONFLICT : ST_FAILED;  // nothing left to spawn
+    uint32_t g = head;
+    if (SORTED) {
+      uint32_t best = G[head].skey;
+      for (uint32_t q = head + 1; q < ng; q++) {
+        Group gq = G[q];
+        if (gq.next < B && gq.skey < best) { best = gq.skey; g = q; }
+      }
+    }
+    Group gr = G[g];
+    uint32_t s = gr.next;
+    G[g].next = (uint8_t)(s + 1);
+    if ((gr.meta >> s) & 1u) {  // claimed by another insertion: ignore it (Sec. 8)
+      c.foreign = 1;
+      continue;
+    }
+    uint64_t rec = ld_slot(t.slots + (uint64_t)gr.bin * B + s);
+    if (rec == EMPTY) continue;
+    uint32_t y = other_bin2(t, rec, gr.bin);
+    if (vis_has(vis, gen, y)) continue;
+    if (SORTED && spawn_of(gr.meta) < 15) {
+      uint32_t nm = gr.meta + (1u << SPAWN_SHIFT);
+      if (cas_acquire(t.meta + gr.bin, gr.meta, nm)) {
+        G[g].meta = nm;
+      } else {
+        G[g].stale = 1;
+        uint32_t m = ld_acquire(t.meta + gr.bin);
+        for (int k = 0; k < 64 && spawn_of(m) < 15; k++) {  // bounded: a lost count is harmless
+          if (cas_acquire(t.meta + gr.bin, m, m + (1u << SPAWN_SHIFT))) break;
+          m = ld_acquire(t.meta + gr.bin);
+        }
+      }
+    }
+    if (c.viewed - c.viewed0 >= t.cap || ng >= MAX_GROUPS)  // budget spent
+      return c.foreign ? ST_CONFLICT : ST_FAILED;
+    View<B> vy;
+    load_view<B>(t, y, vy);
+    c.viewed++;
+    if (claimed_mask<B>(vy)) c.foreign = 1;
+    uint32_t fm = free_mask<B>(vy);
+    int term = lowest(fm);
+    bool isdup = false;
+    if (term < 0 && GHOST) {
+      term = lowest(dup_mask<B>(vy));
+      isdup = term >= 0;
+    }
+    if (term < 0) {
+      push(y, vy.m, (g << 3) | s);
+      continue;
+    }
+    // path root -> ... -> (g, s): depth entries in chain order
+    uint32_t depth = 1;
+    for (uint32_t q = g; G[q].parent != ~0u; q = G[q].parent >> 3) depth++;
+    if ((int)depth + 4 > c.plan->cap) return ST_LONG;
+    Plan& p = *c.plan;
+    {
+      uint32_t q = g, qs = s;
+      for (int i = (int)depth - 1; i >= 0; i--) {
+        p.bin[i] = G[q].bin;
+        p.slot[i] = (uint8_t)qs;
+        p.kind[i] = K_MOVE;
+        p.hit[i] = 0;
+        p.old_r[i] = p.new_r[i] = 0;
+        p.content[i] = q;  // group index until the slot is claimed
+        uint32_t par = G[q].parent;
+        if (par != ~0u) { qs = par & 7u; q = par >> 3; }
+      }
+    }
+    // claim the path in chain order; each CAS checks its bin is as viewed,
+    // so the record read after the claim is the one the search saw
+    p.n = 0;
+    for (uint32_t i = 0; i < depth; i++) {
+      Group gq = G[(uint32_t)p.content[i]];
+      if (gq.stale) return ST_CONFLICT;
+      if (!cas_acquire(t.meta + gq.bin, gq.meta, gq.meta + (1u << p.slot[i]))) return ST_CONFLICT;
+      p.n = (int)i + 1;
+      p.content[i] = ld_slot(t.slots + (uint64_t)gq.bin * B + p.slot[i]);
+    }
+    c.kicks = depth;
+    if (isdup) return take_dup<B>(t, c, y, vy, term, false);
+    return take_free<B>(t, c, y, vy, term, false);
+  }
+}
+
+}  // namespace ck

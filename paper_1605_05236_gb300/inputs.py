@@ -7,15 +7,23 @@ any of the computation under test.
 
 Recipe (the paper uses "uniformly randomly generated hashes" and keys that
 are absent when inserted, Sec. 3):
-  * keys: the SplitMix64 stream seeded with `seed`, high 32 bits of each
-    output; 0xFFFFFFFF (the empty-slot marker) and repeats are dropped, so
-    the first n survivors are n distinct uniform uint32 keys;
+  * key stream of seed s: SplitMix64 seeded with s, high 32 bits of each
+    output; 0xFFFFFFFF (the empty-slot marker), repeats and excluded keys
+    are skipped, so the first n survivors are n distinct uniform uint32 keys;
   * value of key k: k * 2654435761 mod 2^32;
-  * absent keys for lookups continue the same stream, skipping keys that
-    were inserted;
-  * orders are random permutations: argsort of a second SplitMix64 stream.
+  * absent keys for lookups continue the same stream after the inserted
+    keys, skipping every inserted key;
+  * orders: forward Fisher-Yates shuffles driven by the stream of another
+    seed (position i swaps with i + out_i mod (n - i)).
+
+The work is done by inputs_gen.c (compiled with gcc on first use); the
+``ref_*`` functions restate it in numpy/Python for tests on small sizes.
 """
 from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
 
 import numpy as np
 
@@ -23,6 +31,38 @@ RESERVED_KEY = 0xFFFFFFFF
 GOLDEN_GAMMA = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "inputs_gen.c")
+_LIB = os.path.join(_HERE, "_build", "libckgen.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _gen():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        L.gen_distinct_keys.restype = ctypes.c_int64
+        L.gen_distinct_keys.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
+                                        ctypes.c_uint64, ctypes.c_void_p]
+        L.gen_permutation.restype = ctypes.c_int
+        L.gen_permutation.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p]
+        L.gen_gather_u32.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None and len(a) else None
 
 
 def splitmix64_stream(seed: int, start: int, count: int) -> np.ndarray:
@@ -36,36 +76,26 @@ def splitmix64_stream(seed: int, start: int, count: int) -> np.ndarray:
         return z ^ (z >> np.uint64(31))
 
 
-def _first_distinct(cand: np.ndarray, exclude: np.ndarray | None) -> np.ndarray:
-    """Candidates in order of first appearance, without repeats, without the
-    reserved key and without anything in `exclude`."""
-    _, first = np.unique(cand, return_index=True)
-    first.sort()
-    out = cand[first]
-    out = out[out != np.uint32(RESERVED_KEY)]
-    if exclude is not None and len(exclude):
-        out = out[~np.isin(out, exclude, assume_unique=False)]
-    return out
-
-
 def distinct_keys(n: int, seed: int, exclude: np.ndarray | None = None,
                   start: int = 0) -> tuple[np.ndarray, int]:
     """n distinct uint32 keys from the stream of `seed` beginning at output
-    `start`; returns (keys, next_start)."""
-    got = np.empty(0, dtype=np.uint32)
-    pos = start
-    while len(got) < n:
-        need = n - len(got)
-        m = int(need * 1.02) + 1024
-        cand = (splitmix64_stream(seed, pos, m) >> np.uint64(32)).astype(np.uint32)
-        pos += m
-        if len(got):
-            ex = got if exclude is None else np.concatenate([exclude, got])
-        else:
-            ex = exclude
-        got = np.concatenate([got, _first_distinct(cand, ex)])
-    # trim to exactly n, and report where the stream position of the nth key is
-    return got[:n].copy(), pos
+    `start`, skipping `exclude`; returns (keys, stream index after the last key)."""
+    out = np.empty(n, dtype=np.uint32)
+    ex = None if exclude is None else np.ascontiguousarray(exclude, dtype=np.uint32)
+    nxt = _gen().gen_distinct_keys(seed & 0xFFFFFFFFFFFFFFFF, start, n, _p(ex), 0 if ex is None else len(ex),
+                                   _p(out))
+    if nxt < 0:
+        raise MemoryError("key generator: out of memory")
+    return out, int(nxt)
+
+
+def permutation(n: int, seed: int, k: int | None = None) -> np.ndarray:
+    """The first k (default n) entries of a forward Fisher-Yates shuffle of range(n)."""
+    k = n if k is None else min(k, n)
+    out = np.empty(k, dtype=np.uint64)
+    if _gen().gen_permutation(seed & 0xFFFFFFFFFFFFFFFF, n, k, _p(out)) != 0:
+        raise MemoryError("permutation: out of memory")
+    return out.astype(np.int64)
 
 
 def values_for(keys: np.ndarray) -> np.ndarray:
@@ -73,33 +103,50 @@ def values_for(keys: np.ndarray) -> np.ndarray:
         return (keys.astype(np.uint64) * np.uint64(2654435761) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
 
 
-def permutation(n: int, seed: int) -> np.ndarray:
-    """A uniformly random permutation of range(n): argsort of n stream outputs."""
-    return np.argsort(splitmix64_stream(seed, 0, n), kind="stable")
-
-
 def lookup_keys(inserted: np.ndarray, n: int, seed: int, hit_fraction: float = 0.5,
                 next_start: int = 0) -> tuple[np.ndarray, np.ndarray]:
-    """n lookup keys: round(n*hit_fraction) present keys drawn without
-    repetition from `inserted` (in a random order) and the rest absent keys
-    that continue the key stream; shuffled together.  Returns (keys,
-    expected_present)."""
-    n_hit = int(round(n * hit_fraction))
-    n_hit = min(n_hit, len(inserted)) if len(inserted) else 0
-    perm = permutation(len(inserted), seed + 1000)[:n_hit]
-    present = inserted[perm]
+    """n lookup keys: round(n*hit_fraction) distinct present keys drawn from
+    `inserted` and the rest absent keys continuing the key stream of `seed`
+    at `next_start`; shuffled together.  Returns (keys, expected_present)."""
+    n_hit = min(int(round(n * hit_fraction)), len(inserted))
+    present = inserted[permutation(len(inserted), seed + 1000, n_hit)]
     absent, _ = distinct_keys(n - n_hit, seed, exclude=inserted, start=next_start)
     keys = np.concatenate([present, absent])
     flag = np.concatenate([np.ones(n_hit, np.uint8), np.zeros(n - n_hit, np.uint8)])
     order = permutation(n, seed + 2000)
-    return keys[order].copy(), flag[order].copy()
+    return keys[order], flag[order]
 
 
 def delete_keys(inserted: np.ndarray, n: int, seed: int) -> np.ndarray:
     """The first n keys of a random permutation of the inserted set."""
-    return inserted[permutation(len(inserted), seed + 3000)[:n]].copy()
+    return inserted[permutation(len(inserted), seed + 3000, n)]
 
 
 def load_target(slots: int, load: float) -> int:
     """Number of keys that fills `slots` slots to `load` (rounded down)."""
     return int(np.floor(slots * load + 1e-9))
+
+
+# ---- plain restatements for tests (small sizes) ----
+
+def ref_distinct_keys(n, seed, exclude=(), start=0):
+    seen = set(int(x) for x in exclude)
+    out, i = [], start
+    while len(out) < n:
+        k = int(splitmix64_stream(seed, i, 1)[0]) >> 32
+        i += 1
+        if k == RESERVED_KEY or k in seen:
+            continue
+        seen.add(k)
+        out.append(k)
+    return np.array(out, dtype=np.uint32), i
+
+
+def ref_permutation(n, seed, k=None):
+    k = n if k is None else min(k, n)
+    a = list(range(n))
+    outs = splitmix64_stream(seed, 0, max(n, 1))
+    for i in range(min(k, n - 1) if n else 0):
+        j = i + int(outs[i]) % (n - i)
+        a[i], a[j] = a[j], a[i]
+    return np.array(a[:k], dtype=np.int64)

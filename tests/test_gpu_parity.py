@@ -1,0 +1,188 @@
+"""GPU parity: the CUDA path (through the C ABI) against the serial oracle.
+
+* Serial replay (one insertion in flight, keys in batch order): the slot
+  layout, the policy's metadata (duplicate marks, hit counters, spawn
+  counts, rattle counters), every per-key status and every per-key count of
+  bins viewed equal the oracle's exactly.
+* Concurrent batches: the key->value map, every lookup and every delete
+  result equal the oracle's exactly (the layout may differ); the table
+  passes the structural invariants; the mean bins viewed per insertion is
+  within 10% of the oracle's at the same load.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1605_05236_gb300 import ck, inputs
+from table_checks import check_table
+
+pytestmark = pytest.mark.gpu
+
+EMPTY = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+TWO_CHOICE = [ck.RANDOM, ck.BFS, ck.SORTED, ck.QUEUE, ck.RANDOM | ck.GHOST, ck.BFS | ck.GHOST,
+              ck.SORTED | ck.GHOST, ck.QUEUE | ck.GHOST]
+
+
+def pname(p):
+    base = {0: "random", 1: "bfs", 2: "sorted", 3: "queue", 4: "rattle"}[p & 0xFF]
+    return base + ("+ghost" if p & ck.GHOST else "")
+
+
+def fill_case(bins, B, d, load, seed):
+    n = inputs.load_target(bins * B, load)
+    keys, nxt = inputs.distinct_keys(n, seed)
+    return keys, inputs.values_for(keys), nxt
+
+
+def meta_fields(meta, B, d):
+    meta = meta.astype(np.uint32)
+    if d > 2:
+        return {"rattle": ((meta >> 8) & 0xFF).astype(np.uint8)}
+    dup = np.zeros(len(meta) * B, dtype=np.uint8)
+    for s in range(B):
+        dup[s::B] = (meta >> (8 + s)) & 1
+    return {"dup": dup, "spawn": ((meta >> 16) & 0xF).astype(np.uint8),
+            "hit": ((meta >> 20) & 0xFF).astype(np.uint8)}
+
+
+SERIAL_CASES = (
+    [(1 << 14, 4, 2, p, 0.95) for p in TWO_CHOICE]            # 2^14 bins x 4 slots to 0.95
+    + [(1 << 12, 8, 2, p, 0.97) for p in TWO_CHOICE]          # 8-slot bins to 0.97
+    + [(1 << 14, 1, 3, ck.RANDOM, 0.90), (1 << 14, 1, 3, ck.RATTLE, 0.90),
+       (1 << 14, 1, 4, ck.RANDOM, 0.96), (1 << 14, 1, 4, ck.RATTLE, 0.96)]
+)
+
+
+@pytest.mark.parametrize("bins,B,d,policy,load", SERIAL_CASES,
+                         ids=["%dx%d-d%d-%s-%.2f" % (b, s, d, pname(p), l) for b, s, d, p, l in SERIAL_CASES])
+def test_serial_replay_matches_oracle_exactly(bins, B, d, policy, load):
+    keys, vals, _ = fill_case(bins, B, d, load, 1)
+    cap = 500
+    ref = oracle.OracleTable(bins, B, d, policy, rng_seed=7, cap=cap)
+    ost, oviewed, _ = ref.insert(keys, vals, trace=True)
+    t = ck.CuckooTable(bins, B, d, policy, seed=7)
+    t.set_param(ck.PARAM_CHAIN_CAP, cap)
+    viewed = torch.zeros(len(keys), dtype=torch.int32, device="cuda")
+    st = t.insert(ck.as_u32_tensor(keys), ck.as_u32_tensor(vals), viewed=viewed, serial=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(st.cpu().numpy(), ost)
+    assert np.array_equal(ck.u32_numpy(viewed), oviewed)
+    slots, meta = t.export()
+    e = ref.export()
+    assert np.array_equal(slots, e["rec"])
+    f = meta_fields(meta, B, d)
+    if d > 2:
+        if policy == ck.RATTLE:
+            assert np.array_equal(f["rattle"], e["rattle"])
+    else:
+        assert np.array_equal(f["dup"], e["dup"])
+        if policy & 0xFF == ck.QUEUE:
+            assert np.array_equal(f["hit"], e["hit"])
+        if policy & 0xFF == ck.SORTED:
+            assert np.array_equal(f["spawn"], e["spawn"])
+    s, os_ = t.stats(), ref.stats()
+    for k in ("inserts_ok", "inserts_failed", "bins_viewed", "kicks", "chain_max", "ghost_pairs_made",
+              "dup_evictions", "size", "live_ghosts"):
+        assert s[k] == os_[k], k
+    check_table(slots, meta, bins, B, d)
+
+
+CONCURRENT_CASES = (
+    [(1 << 16, 4, 2, p, 0.95) for p in TWO_CHOICE]
+    + [(1 << 15, 8, 2, p, 0.97) for p in (ck.RANDOM, ck.QUEUE, ck.SORTED | ck.GHOST)]
+    + [(1 << 18, 1, 3, ck.RANDOM, 0.90), (1 << 16, 1, 4, ck.RATTLE, 0.96), (1 << 16, 1, 4, ck.RANDOM, 0.96)]
+)
+
+
+@pytest.mark.parametrize("bins,B,d,policy,load", CONCURRENT_CASES,
+                         ids=["%dx%d-d%d-%s-%.2f" % (b, s, d, pname(p), l) for b, s, d, p, l in CONCURRENT_CASES])
+def test_concurrent_set_semantics_match_oracle(bins, B, d, policy, load):
+    keys, vals, nxt = fill_case(bins, B, d, load, 3)
+    cap = 4000 if (d > 2 and policy == ck.RANDOM) else 500
+    ref = oracle.OracleTable(bins, B, d, policy, rng_seed=7, cap=min(cap, 10 ** 6))
+    ost = ref.insert(keys, vals)
+    assert (ost == 0).all()
+    t = ck.CuckooTable(bins, B, d, policy, seed=7)
+    t.set_param(ck.PARAM_CHAIN_CAP, cap)
+    kt, vt = ck.as_u32_tensor(keys), ck.as_u32_tensor(vals)
+    # batches of 1/64 of the slots, the ratio of 2^20-key batches to a 2^26-slot
+    # table, plus a ragged tail
+    batch = max(1024, (bins * B) // 64)
+    sts = []
+    for lo in range(0, len(keys), batch):
+        sts.append(t.insert(kt[lo:lo + batch], vt[lo:lo + batch]))
+    st = torch.cat(sts).cpu().numpy()
+    assert (st == 0).all(), np.bincount(st)
+    slots, meta = t.export()
+    info = check_table(slots, meta, bins, B, d)
+    assert info["size"] == len(keys)
+    assert t.contents() == ref.contents()
+    s, os_ = t.stats(), ref.stats()
+    assert s["size"] == len(keys) and s["live_ghosts"] == info["ghost_pairs"]
+    # bins viewed per insertion: within 10% of the serial oracle at the same load
+    assert abs(s["bins_viewed"] / os_["bins_viewed"] - 1) < 0.10, (s["bins_viewed"], os_["bins_viewed"])
+    # lookups, 50% present / 50% absent
+    probe, expect = inputs.lookup_keys(keys, 1 << 16, 9, 0.5, next_start=nxt)
+    v, fnd = t.lookup(ck.as_u32_tensor(probe))
+    ov, of = ref.lookup(probe)
+    assert np.array_equal(fnd.cpu().numpy(), of) and np.array_equal(of, expect)
+    assert np.array_equal(ck.u32_numpy(v), ov)
+    # deletes of present keys and of absent keys
+    dk = np.concatenate([inputs.delete_keys(keys, len(keys) // 8, 4), probe[expect == 0][:1000]])
+    fd = t.delete(ck.as_u32_tensor(dk)).cpu().numpy()
+    assert np.array_equal(fd, ref.delete(dk))
+    assert t.contents() == ref.contents()
+    slots, meta = t.export()
+    assert check_table(slots, meta, bins, B, d)["size"] == ref.stats()["size"]
+    # re-insert half of the deleted keys after the deletes
+    back = dk[: len(keys) // 16]
+    st2 = t.insert(ck.as_u32_tensor(back), ck.as_u32_tensor(inputs.values_for(back))).cpu().numpy()
+    assert (st2 == 0).all() and (ref.insert(back, inputs.values_for(back)) == 0).all()
+    assert t.contents() == ref.contents()
+
+
+def test_edge_cases_empty_ragged_reserved():
+    t = ck.CuckooTable(1 << 10, 4, 2, ck.RANDOM, seed=1)
+    ref = oracle.OracleTable(1 << 10, 4, 2, ck.RANDOM, rng_seed=1)
+    empty = torch.empty(0, dtype=torch.int32, device="cuda")
+    t.insert(empty, empty)
+    t.lookup(empty)
+    t.delete(empty)
+    keys, _ = inputs.distinct_keys(3000, 17)
+    keys[5] = 0xFFFFFFFF
+    vals = inputs.values_for(keys)
+    for lo, hi in ((0, 1), (1, 32), (32, 33), (33, 290), (290, 3000)):  # ragged batch sizes
+        st = t.insert(ck.as_u32_tensor(keys[lo:hi]), ck.as_u32_tensor(vals[lo:hi])).cpu().numpy()
+        ost = ref.insert(keys[lo:hi], vals[lo:hi])
+        assert np.array_equal(st == 3, ost == 3)
+        assert (st[ost != 3] == 0).all()
+    assert t.contents() == ref.contents()
+    v, f = t.lookup(ck.as_u32_tensor(np.array([0xFFFFFFFF, keys[0], keys[5]], dtype=np.uint32)))
+    assert list(f.cpu().numpy()) == [0, 1, 0]
+
+
+@pytest.mark.parametrize("policy", [ck.RANDOM, ck.QUEUE, ck.BFS, ck.SORTED | ck.GHOST])
+def test_overfull_table_failures_are_clean(policy):
+    """A table pushed past its capacity: failed keys are absent, every other
+    key is present once, and the serial replay fails exactly the oracle's keys."""
+    bins, B = 256, 4
+    keys, _ = inputs.distinct_keys(bins * B + 200, 23)
+    vals = inputs.values_for(keys)
+    ref = oracle.OracleTable(bins, B, 2, policy, rng_seed=2, cap=100)
+    ost = ref.insert(keys, vals)
+    ts = ck.CuckooTable(bins, B, 2, policy, seed=2)
+    ts.set_param(ck.PARAM_CHAIN_CAP, 100)
+    st = ts.insert(ck.as_u32_tensor(keys), ck.as_u32_tensor(vals), serial=True).cpu().numpy()
+    assert np.array_equal(st, ost) and (ost == 1).any()
+    assert ts.contents() == ref.contents()
+    tc = ck.CuckooTable(bins, B, 2, policy, seed=2)
+    tc.set_param(ck.PARAM_CHAIN_CAP, 100)
+    st = tc.insert(ck.as_u32_tensor(keys), ck.as_u32_tensor(vals)).cpu().numpy()
+    got = tc.contents()
+    ok = {int(k): int(v) for k, v, s in zip(keys, vals, st) if s == 0}
+    assert got == ok
+    slots, meta = tc.export()
+    check_table(slots, meta, bins, B, 2)
+    assert tc.stats()["size"] == len(ok)
