@@ -71,6 +71,9 @@ extern "C" {
                                            concurrently read key is never absent (Sec. 8) */
 #define CK_PARAM_OVERLAP 32     /* 1 (default): an insert launch may start while the previous
                                    one on the stream finishes its longest chains */
+#define CK_PARAM_HASH_FAMILY 33 /* 0 (default): h_i = fmix32(k ^ seed_i); 1: decorrelated
+                                   h_i = fmix32(fmix32(k + seed_i) ^ (seed_i * 0x27D4EB2F)).
+                                   Set before the first insertion. */
 
 /* ---- ck_insert_batch_ex flags ---- */
 #define CK_INS_SERIAL 1  /* one insertion in flight, keys in batch order (debug/parity) */
@@ -80,7 +83,8 @@ typedef struct ck_stats_t {
   uint64_t inserts_ok;
   uint64_t inserts_failed;      /* CK_ST_FAILED */
   uint64_t inserts_aborted;     /* CK_ST_ABORTED */
-  uint64_t bins_viewed;         /* every bin whose slots an insertion examined (Sec. 3 metric) */
+  uint64_t bins_viewed;         /* bins examined by the attempt of each insertion that was
+                                   applied or failed (the Sec. 3 metric) */
   uint64_t kicks;               /* records displaced by successful insertions */
   uint64_t chain_max;           /* longest kick-out chain */
   uint64_t aborts;              /* attempts abandoned on a claim conflict (Sec. 8) */
@@ -90,7 +94,8 @@ typedef struct ck_stats_t {
   uint64_t live_ghosts;         /* live ghost pairs */
   uint64_t lookups, lookup_hits;
   uint64_t deletes, delete_hits, delete_aborts;
-  uint64_t conflict_views;      /* bins viewed again after a lost claim race (included in bins_viewed) */
+  uint64_t conflict_views;      /* bins viewed again after a lost claim race */
+  uint64_t bins_viewed_all;     /* bins examined by all attempts, abandoned ones included */
   uint64_t total_slots;         /* n_bins * B */
   double load;                  /* size / total_slots */
   double bins_viewed_per_insert;/* bins_viewed / (inserts_ok + failed + aborted) */

@@ -77,6 +77,7 @@ def lib():
         L.orc_set_bins_override.restype = ctypes.c_int
         L.orc_set_bins_override.argtypes = [ctypes.c_void_p, u32p, u64p, ctypes.c_uint64]
         L.orc_set_rattle_tie_resident.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.orc_set_hash_family.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.orc_bins.argtypes = [ctypes.c_void_p, ctypes.c_uint32, u64p]
         L.orc_fmix32.restype = ctypes.c_uint32
         L.orc_fmix32.argtypes = [ctypes.c_uint32]
@@ -136,6 +137,9 @@ class OracleTable:
                                          _ptr(bins, ctypes.c_uint64), len(keys))
         if rc != 0:
             raise ValueError("bad bin override")
+
+    def set_hash_family(self, family: int):
+        lib().orc_set_hash_family(self._h, int(family))
 
     def set_rattle_tie_resident(self, on: bool):
         lib().orc_set_rattle_tie_resident(self._h, 1 if on else 0)

@@ -99,6 +99,7 @@ typedef struct orc_table {
   uint32_t ghost;      /* ghost insertions on (Sec. 4) */
   uint32_t cap;        /* kick-out cap (walks), try cap (rattle), bin budget (search) */
   uint32_t rattle_tie_resident; /* debug reading: resident wins rattle ties */
+  uint32_t hash_family;  /* 0: fmix32(key ^ seed_i); 1: fmix32(fmix32(key + seed_i) ^ seed_i*0x27D4EB2F) */
   uint64_t rng_seed;
   uint32_t seeds[4];
 
@@ -181,9 +182,12 @@ static int ov_find(const orc_table *t, uint32_t key) {
 }
 
 /* The d bins of a key (Sec. 1: "maps each key to two distinct bins";
- * Sec. 7 for d hash functions).  h_i = fmix32(key ^ seed_i) mod n.  A
- * collision with an earlier choice moves to the next bin (mod n), so the d
- * choices are distinct as the paper requires. */
+ * Sec. 7 for d hash functions).  h_i = fmix32(key ^ seed_i) mod n (family
+ * 0, the stated workload's hash), or, in family 1, a decorrelated form of
+ * the same mix: fmix32(fmix32(key + seed_i) ^ (seed_i * 0x27D4EB2F)) mod n
+ * (family 0's functions are not independent: key ^ seed_i ^ seed_j gets
+ * key's h_i and h_j swapped).  A collision with an earlier choice moves to
+ * the next bin (mod n), so the d choices are distinct as the paper requires. */
 static void bins_of(const orc_table *t, uint32_t key, uint64_t *out) {
   if (t->n_ov) {
     int i = ov_find(t, key);
@@ -193,7 +197,9 @@ static void bins_of(const orc_table *t, uint32_t key, uint64_t *out) {
     }
   }
   for (uint32_t i = 0; i < t->d; i++) {
-    uint64_t b = (uint64_t)fmix32(key ^ t->seeds[i]) % t->n;
+    uint32_t s = t->seeds[i];
+    uint32_t h = t->hash_family ? fmix32(fmix32(key + s) ^ (uint32_t)(s * 0x27D4EB2Fu)) : fmix32(key ^ s);
+    uint64_t b = (uint64_t)h % t->n;
     for (;;) {
       int clash = 0;
       for (uint32_t j = 0; j < i; j++) if (out[j] == b) clash = 1;
@@ -271,6 +277,7 @@ void orc_destroy(orc_table *t) {
 }
 
 void orc_set_rattle_tie_resident(orc_table *t, int on) { t->rattle_tie_resident = on ? 1 : 0; }
+void orc_set_hash_family(orc_table *t, int f) { t->hash_family = f ? 1 : 0; }
 
 /* Fixtures: give `n` keys explicit bin choices (d per key, distinct). */
 int orc_set_bins_override(orc_table *t, const uint32_t *keys, const uint64_t *bins, uint64_t n) {

@@ -25,7 +25,7 @@ GHOST = 0x100
 # parameters
 PARAM_CHAIN_CAP, PARAM_MAX_RETRIES, PARAM_RNG_SEED = 1, 2, 3
 PARAM_HASH_SEED0, PARAM_BLOCK = 10, 20
-PARAM_RATTLE_TIE_RESIDENT, PARAM_ORDERED_WRITES, PARAM_OVERLAP = 30, 31, 32
+PARAM_RATTLE_TIE_RESIDENT, PARAM_ORDERED_WRITES, PARAM_OVERLAP, PARAM_HASH_FAMILY = 30, 31, 32, 33
 INS_SERIAL = 1
 HIST_BUCKETS = 200
 
@@ -36,7 +36,8 @@ class CkStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "inserts_ok", "inserts_failed", "inserts_aborted", "bins_viewed", "kicks", "chain_max",
         "aborts", "ghost_pairs_made", "dup_evictions", "size", "live_ghosts", "lookups",
-        "lookup_hits", "deletes", "delete_hits", "delete_aborts", "conflict_views", "total_slots")] + [
+        "lookup_hits", "deletes", "delete_hits", "delete_aborts", "conflict_views", "bins_viewed_all",
+        "total_slots")] + [
         ("load", ctypes.c_double), ("bins_viewed_per_insert", ctypes.c_double),
         ("aborts_per_insert", ctypes.c_double)]
 

@@ -34,6 +34,7 @@ constexpr int LONG_CHAIN = 4104;  // plan entries of a scratch-backed plan (walk
 constexpr int LONG_REGION = 69888;  // bytes of one scratch plan (17 * LONG_CHAIN, 256-aligned)
 constexpr int MAX_GROUPS = 512;   // bins a search can view (budget <= MAX_GROUPS)
 constexpr int VISITED_SLOTS = 1024;
+constexpr int SLAB = 256;         // search regions per slab (one slab per block, blockDim <= SLAB)
 
 constexpr uint32_t DUP_SHIFT = 8;
 constexpr uint32_t SPAWN_SHIFT = 16;
@@ -52,7 +53,7 @@ enum Status : int { ST_OK = 0, ST_FAILED = 1, ST_ABORTED = 2, ST_INVALID = 3, ST
 enum Counter : int {
   C_INS_OK = 0, C_INS_FAILED, C_INS_ABORTED, C_VIEWED, C_KICKS, C_CHAIN_MAX, C_ABORTS,
   C_GHOSTS_MADE, C_DUP_EVICT, C_SIZE, C_LIVE_GHOSTS /* C_SIZE + 1 */, C_LOOKUPS, C_LOOKUP_HITS, C_DELETES,
-  C_DELETE_HITS, C_DELETE_ABORTS, C_REVIEWS, C_N = 24
+  C_DELETE_HITS, C_DELETE_ABORTS, C_REVIEWS, C_VIEWED_ALL, C_N = 24
 };
 constexpr int HIST_BUCKETS = 200;
 
@@ -63,6 +64,7 @@ struct DevTable {
   uint8_t* scratch;              // search scratch, SEARCH_REGION bytes per searcher
   uint8_t* long_scratch;         // n_long plans of LONG_REGION bytes
   uint32_t* long_busy;           // n_long flags: plan region in use
+  uint32_t* slab_busy;           // n_searchers / SLAB flags: a block's slab of search regions is in use
   uint64_t n_bins;
   uint64_t total_slots;
   uint64_t rng_seed;
@@ -72,6 +74,7 @@ struct DevTable {
   uint32_t ordered_writes, tie_resident;
   uint32_t n_searchers;
   uint32_t n_long;
+  uint32_t hash_family;          // 0: fmix32(k ^ seed_i); 1: decorrelated (see bin_hash)
   uint32_t seeds[4];
 };
 
@@ -111,12 +114,23 @@ __device__ __forceinline__ uint32_t next_bin(const DevTable& t, uint32_t b) {
   return (uint64_t)(b + 1) == t.n_bins ? 0u : b + 1;
 }
 
-// The d bins of a key: h_i = fmix32(key ^ seed_i) mod n_bins; a choice equal
-// to an earlier one moves to the next bin, so the choices are distinct (Sec. 1).
+// Hash i of a key.  Family 0: fmix32(key ^ seed_i), the stated workload's
+// hash.  Its d functions are not independent: key ^ seed_i ^ seed_j has
+// key's h_i and h_j swapped, so such pairs share two bins, which single-slot
+// d-ary tables feel at scale.  Family 1 keeps fmix32 but decorrelates the
+// functions: fmix32(fmix32(key + seed_i) ^ (seed_i * 0x27D4EB2F)), closer to
+// the independent uniform hashes the paper assumes (Sec. 3).
+__device__ __forceinline__ uint32_t bin_hash(const DevTable& t, uint32_t key, uint32_t i) {
+  uint32_t s = t.seeds[i];
+  return t.hash_family ? fmix32(fmix32(key + s) ^ (s * 0x27D4EB2Fu)) : fmix32(key ^ s);
+}
+
+// The d bins of a key: h_i mod n_bins; a choice equal to an earlier one
+// moves to the next bin, so the choices are distinct (Sec. 1).
 __device__ __forceinline__ void bins_of(const DevTable& t, uint32_t key, uint32_t* b) {
-  b[0] = reduce_bin(t, fmix32(key ^ t.seeds[0]));
+  b[0] = reduce_bin(t, bin_hash(t, key, 0));
   for (uint32_t i = 1; i < t.d; i++) {
-    uint32_t x = reduce_bin(t, fmix32(key ^ t.seeds[i]));
+    uint32_t x = reduce_bin(t, bin_hash(t, key, i));
     for (;;) {
       bool clash = false;
       for (uint32_t j = 0; j < i; j++) clash |= (b[j] == x);
@@ -128,8 +142,8 @@ __device__ __forceinline__ void bins_of(const DevTable& t, uint32_t key, uint32_
 }
 
 __device__ __forceinline__ void bins2(const DevTable& t, uint32_t key, uint32_t& b0, uint32_t& b1) {
-  b0 = reduce_bin(t, fmix32(key ^ t.seeds[0]));
-  b1 = reduce_bin(t, fmix32(key ^ t.seeds[1]));
+  b0 = reduce_bin(t, bin_hash(t, key, 0));
+  b1 = reduce_bin(t, bin_hash(t, key, 1));
   if (b1 == b0) b1 = next_bin(t, b1);
 }
 

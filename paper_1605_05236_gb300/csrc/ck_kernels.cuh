@@ -53,6 +53,26 @@ __device__ __forceinline__ void release_long(const DevTable& t, int r) {
   atomicExch(t.long_busy + r, 0u);
 }
 
+// A block's slab of search scratch: SLAB consecutive per-thread regions.
+// Taken at block start and returned at block end, so blocks of overlapping
+// launches never share a region.  A block of the next launch may wait for
+// a slab while the previous launch drains; the wait is bounded (about 10 ms),
+// after which the block reports its keys as aborted.
+__device__ __forceinline__ int acquire_slab(const DevTable& t) {
+  uint32_t n_slabs = t.n_searchers / SLAB;
+  if (n_slabs == 0) return -1;
+  for (uint32_t round = 0; round < 4096; round++) {
+    uint32_t start = (blockIdx.x + round * 7919u) % n_slabs;
+    for (uint32_t k = 0; k < n_slabs; k++) {
+      uint32_t r = start + k;
+      if (r >= n_slabs) r -= n_slabs;
+      if (*(volatile uint32_t*)(t.slab_busy + r) == 0 && atomicCAS(t.slab_busy + r, 0u, 1u) == 0u) return (int)r;
+    }
+    __nanosleep(2000);
+  }
+  return -1;
+}
+
 // One insertion with bounded retries after claim conflicts.  A chain that
 // outgrows the local plan is planned again, with the same draws, in a
 // scratch-backed plan.
@@ -96,8 +116,9 @@ __device__ __forceinline__ int insert_one(const DevTable& t, Ctx& c, uint8_t* re
   return st;
 }
 
-// Insert kernel.  Concurrent mode: a grid-stride loop, one insertion per
-// thread at a time, plans in local memory.  Serial mode (SERIAL, one
+// Insert kernel.  Concurrent mode: each block takes a contiguous range of
+// the batch and its threads pull keys from it, one insertion per thread at
+// a time, plans in local memory.  Serial mode (SERIAL, one
 // thread): keys in batch order, one insertion in flight, a scratch-backed
 // plan; this replays the paper's serial algorithms exactly.
 //
@@ -116,21 +137,40 @@ __global__ void __launch_bounds__(256) k_insert(DevTable t, const uint32_t* __re
   __shared__ unsigned int h_views[HIST_BUCKETS];
   __shared__ unsigned int h_cnt[HIST_BUCKETS];
   __shared__ unsigned long long bc[C_N];
+  __shared__ unsigned long long s_next;  // next key of this block's range
+  __shared__ int s_slab, s_long;
   for (int i = threadIdx.x; i < HIST_BUCKETS; i += blockDim.x) h_views[i] = h_cnt[i] = 0;
   for (int i = threadIdx.x; i < C_N; i += blockDim.x) bc[i] = 0;
+  // each block owns a contiguous range of the batch; its threads pull keys
+  // from it one at a time, so a thread held up by a long chain does not
+  // hold up the others
+  const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const uint64_t lo = min(n, (uint64_t)blockIdx.x * per), hi = min(n, lo + per);
+  if (threadIdx.x == 0) {
+    s_next = lo;
+    s_slab = t.scratch ? acquire_slab(t) : -1;
+    s_long = SERIAL ? acquire_long(t, 0) : -1;
+  }
   __syncthreads();
 
   PlanStore<SERIAL ? 1 : MAX_CHAIN> store;
-  Plan local = SERIAL ? plan_in(t.long_scratch) : store.view();
-  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  uint8_t* region = t.scratch ? t.scratch + tid * SEARCH_REGION : nullptr;
+  Plan local = store.view();
+  bool usable = true;
+  if (SERIAL) {
+    if (s_long >= 0) local = plan_in(t.long_scratch + (uint64_t)s_long * LONG_REGION);
+    else usable = false;
+  }
+  uint8_t* region = s_slab >= 0 ? t.scratch + ((uint64_t)s_slab * SLAB + threadIdx.x) * SEARCH_REGION
+                                : nullptr;
+  if (t.scratch && !region) usable = false;
   const unsigned long long size_base = load_base;
 
   unsigned long long ok = 0, failed = 0, aborted = 0, viewed = 0, kicks = 0, ghosts = 0, dupev = 0;
-  unsigned long long reviews = 0;
+  unsigned long long reviews = 0, viewed_all = 0;
   uint32_t aborts = 0, chain_max = 0;
-  for (uint64_t i = tid; i < n; i += stride) {
+  for (;;) {
+    uint64_t i = atomicAdd(&s_next, 1ull);
+    if (i >= hi) break;
     uint32_t key = keys[i];
     if (key == RESERVED_KEY) {
       if (status) status[i] = ST_INVALID;
@@ -142,7 +182,7 @@ __global__ void __launch_bounds__(256) k_insert(DevTable t, const uint32_t* __re
     c.krec = ((uint64_t)key << 32) | vals[i];
     c.viewed = 0;
     c.reviews = 0;
-    int st = insert_one<B, POL, GHOST>(t, c, region, aborts, local);
+    int st = usable ? insert_one<B, POL, GHOST>(t, c, region, aborts, local) : (int)ST_ABORTED;
     if (st == ST_OK) {
       ok++;
       kicks += c.kicks;
@@ -154,13 +194,17 @@ __global__ void __launch_bounds__(256) k_insert(DevTable t, const uint32_t* __re
     } else {
       aborted++;
     }
-    viewed += c.viewed;
+    // bins viewed by the attempt that was applied (or failed), and by all
+    // attempts including those abandoned after claim conflicts
+    uint32_t v_final = c.viewed - c.viewed0;
+    viewed += v_final;
+    viewed_all += c.viewed;
     reviews += c.reviews;
     if (status) status[i] = (uint8_t)st;
-    if (viewed_out) viewed_out[i] = c.viewed;
+    if (viewed_out) viewed_out[i] = v_final;
     uint64_t bucket = ((size_base + i) * HIST_BUCKETS) / t.total_slots;
     if (bucket >= HIST_BUCKETS) bucket = HIST_BUCKETS - 1;
-    atomicAdd(&h_views[bucket], c.viewed);
+    atomicAdd(&h_views[bucket], v_final);
     atomicAdd(&h_cnt[bucket], 1u);
   }
   flush_counter(&bc[C_INS_OK], ok);
@@ -172,6 +216,7 @@ __global__ void __launch_bounds__(256) k_insert(DevTable t, const uint32_t* __re
   flush_counter(&bc[C_GHOSTS_MADE], ghosts);
   flush_counter(&bc[C_DUP_EVICT], dupev);
   flush_counter(&bc[C_REVIEWS], reviews);
+  flush_counter(&bc[C_VIEWED_ALL], viewed_all);
   if (chain_max) atomicMax(&bc[C_CHAIN_MAX], (unsigned long long)chain_max);
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -191,6 +236,10 @@ __global__ void __launch_bounds__(256) k_insert(DevTable t, const uint32_t* __re
       atomicAdd(hist + i, (unsigned long long)h_views[i]);
       atomicAdd(hist + HIST_BUCKETS + i, (unsigned long long)h_cnt[i]);
     }
+  }
+  if (threadIdx.x == 0) {
+    if (s_slab >= 0) { __threadfence(); atomicExch(t.slab_busy + s_slab, 0u); }
+    if (s_long >= 0) release_long(t, s_long);
   }
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }

@@ -72,7 +72,7 @@ uint32_t long_plans_for(uint64_t bins) {
 }
 
 struct Layout {
-  size_t slots, meta, counters, busy, long_plans, scratch, total;
+  size_t slots, meta, counters, busy, slab_busy, long_plans, scratch, total;
 };
 
 Layout layout(uint64_t bins, uint32_t B, uint32_t policy) {
@@ -85,6 +85,8 @@ Layout layout(uint64_t bins, uint32_t B, uint32_t policy) {
   off = align_up(off + (C_N + 2 * HIST_BUCKETS) * sizeof(uint64_t));
   L.busy = off;
   off = align_up(off + long_plans_for(bins) * sizeof(uint32_t));
+  L.slab_busy = off;
+  if (is_search(policy)) off = align_up(off + (searchers_for(bins) / SLAB) * sizeof(uint32_t));
   L.long_plans = off;
   off = align_up(off + (size_t)long_plans_for(bins) * LONG_REGION);
   L.scratch = off;
@@ -121,6 +123,7 @@ int init_table(ck_table* t, void* buf, size_t bytes, bool owns, uint64_t bins, u
   dt.scratch = is_search(policy) ? base + L.scratch : nullptr;
   dt.long_scratch = base + L.long_plans;
   dt.long_busy = reinterpret_cast<uint32_t*>(base + L.busy);
+  dt.slab_busy = is_search(policy) ? reinterpret_cast<uint32_t*>(base + L.slab_busy) : nullptr;
   dt.n_long = long_plans_for(bins);
   dt.n_bins = bins;
   dt.total_slots = bins * B;
@@ -163,9 +166,22 @@ cudaError_t launch_insert(const ck_table* t, const uint32_t* keys, const uint32_
     return cudaGetLastError();
   }
   uint32_t block = t->block;
+  // persistent launch: at most the blocks that fit on the GPU at once
+  static int cached_block = 0, cached_per_sm = 0;
+  if (cached_block != (int)block) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_insert<B, POL, GHOST, false>, block, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    cached_per_sm = per_sm;
+    cached_block = (int)block;
+  }
   uint64_t grid = (n + block - 1) / block;
+  uint64_t resident = (uint64_t)cached_per_sm * t->sm_count;
+  if (grid > resident) grid = resident;
   if (t->dt.scratch) {
-    uint64_t cap_blocks = t->dt.n_searchers / block;
+    uint64_t cap_blocks = t->dt.n_searchers / SLAB;
     if (grid > cap_blocks) grid = cap_blocks;
   }
   if (grid > 0x7FFFFFFFull) grid = 0x7FFFFFFFull;
@@ -300,6 +316,10 @@ int ck_set_param(ck_table* t, int key, int64_t value) {
     case CK_PARAM_OVERLAP:
       t->overlap = value ? 1 : 0;
       return CK_OK;
+    case CK_PARAM_HASH_FAMILY:
+      if (value != 0 && value != 1) return CK_EINVAL;
+      d.hash_family = (uint32_t)value;
+      return CK_OK;
     default:
       if (key >= CK_PARAM_HASH_SEED0 && key < CK_PARAM_HASH_SEED0 + (int)d.d) {
         if (value < 0 || value > 0xFFFFFFFFll) return CK_EINVAL;
@@ -378,6 +398,7 @@ int ck_stats(ck_table* t, ck_stats_t* out) {
   out->delete_hits = c[C_DELETE_HITS];
   out->delete_aborts = c[C_DELETE_ABORTS];
   out->conflict_views = c[C_REVIEWS];
+  out->bins_viewed_all = c[C_VIEWED_ALL];
   out->total_slots = t->dt.total_slots;
   out->load = (double)out->size / (double)out->total_slots;
   uint64_t ins = out->inserts_ok + out->inserts_failed + out->inserts_aborted;

@@ -26,11 +26,19 @@ def fmix32_np(h):
     return h
 
 
-def bins_np(keys, n_bins, d):
+def hash_np(keys, i, family):
+    s = np.uint32(SEEDS[i])
+    with np.errstate(over="ignore"):
+        if family == 0:
+            return fmix32_np(keys ^ s)
+        return fmix32_np(fmix32_np(keys + s) ^ (s * np.uint32(0x27D4EB2F)))
+
+
+def bins_np(keys, n_bins, d, family=0):
     keys = keys.astype(np.uint32)
     out = []
     for i in range(d):
-        b = fmix32_np(keys ^ np.uint32(SEEDS[i])).astype(np.uint64) % np.uint64(n_bins)
+        b = hash_np(keys, i, family).astype(np.uint64) % np.uint64(n_bins)
         for _ in range(d):
             clash = np.zeros(len(keys), dtype=bool)
             for j in range(i):
@@ -42,7 +50,7 @@ def bins_np(keys, n_bins, d):
     return np.stack(out, axis=1)
 
 
-def check_table(slots, meta, n_bins, B, d):
+def check_table(slots, meta, n_bins, B, d, family=0):
     """Returns (live key -> value dict-free summary): size, ghost pairs.
     Raises AssertionError on any violated invariant."""
     slots = np.asarray(slots, dtype=np.uint64)
@@ -55,7 +63,7 @@ def check_table(slots, meta, n_bins, B, d):
     recs = slots[idx]
     keys = (recs >> np.uint64(32)).astype(np.uint32)
     here = (idx // B).astype(np.uint64)
-    kb = bins_np(keys, n_bins, d)
+    kb = bins_np(keys, n_bins, d, family)
     mine = (kb == here[:, None]).any(axis=1)
     assert mine.all(), "record outside its bins: key %d" % int(keys[~mine][0])
     if B > 1:

@@ -27,7 +27,19 @@ TWO_CHOICE = [ck.RANDOM, ck.BFS, ck.SORTED, ck.QUEUE, ck.RANDOM | ck.GHOST, ck.B
 
 def pname(p):
     base = {0: "random", 1: "bfs", 2: "sorted", 3: "queue", 4: "rattle"}[p & 0xFF]
-    return base + ("+ghost" if p & ck.GHOST else "")
+    return base + ("+ghost" if p & ck.GHOST else "") + ("+hash1" if p & 0x10000 else "")
+
+
+def make_pair(bins, B, d, policy, seed, cap):
+    """(oracle table, GPU table) with the same shape, policy, draws and hash family."""
+    family = 1 if policy & 0x10000 else 0
+    policy &= 0xFFFF
+    ref = oracle.OracleTable(bins, B, d, policy, rng_seed=seed, cap=cap)
+    ref.set_hash_family(family)
+    t = ck.CuckooTable(bins, B, d, policy, seed=seed)
+    t.set_param(ck.PARAM_CHAIN_CAP, cap)
+    t.set_param(ck.PARAM_HASH_FAMILY, family)
+    return ref, t, family
 
 
 def fill_case(bins, B, d, load, seed):
@@ -51,8 +63,11 @@ SERIAL_CASES = (
     [(1 << 14, 4, 2, p, 0.95) for p in TWO_CHOICE]            # 2^14 bins x 4 slots to 0.95
     + [(1 << 12, 8, 2, p, 0.97) for p in TWO_CHOICE]          # 8-slot bins to 0.97
     + [(1 << 14, 1, 3, ck.RANDOM, 0.90), (1 << 14, 1, 3, ck.RATTLE, 0.90),
-       (1 << 14, 1, 4, ck.RANDOM, 0.96), (1 << 14, 1, 4, ck.RATTLE, 0.96)]
+       (1 << 14, 1, 4, ck.RANDOM, 0.96), (1 << 14, 1, 4, ck.RATTLE, 0.96),
+       (1 << 14, 1, 3, ck.RATTLE | 0x10000, 0.90), (1 << 12, 4, 2, ck.QUEUE | 0x10000, 0.95)]
 )
+# 0x10000 in a case's policy selects the decorrelated hash family (test-only marker)
+FAMILY_FLAG = 0x10000
 
 
 @pytest.mark.parametrize("bins,B,d,policy,load", SERIAL_CASES,
@@ -60,10 +75,9 @@ SERIAL_CASES = (
 def test_serial_replay_matches_oracle_exactly(bins, B, d, policy, load):
     keys, vals, _ = fill_case(bins, B, d, load, 1)
     cap = 500
-    ref = oracle.OracleTable(bins, B, d, policy, rng_seed=7, cap=cap)
+    ref, t, family = make_pair(bins, B, d, policy, 7, cap)
+    policy &= 0xFFFF
     ost, oviewed, _ = ref.insert(keys, vals, trace=True)
-    t = ck.CuckooTable(bins, B, d, policy, seed=7)
-    t.set_param(ck.PARAM_CHAIN_CAP, cap)
     viewed = torch.zeros(len(keys), dtype=torch.int32, device="cuda")
     st = t.insert(ck.as_u32_tensor(keys), ck.as_u32_tensor(vals), viewed=viewed, serial=True)
     torch.cuda.synchronize()
@@ -86,13 +100,15 @@ def test_serial_replay_matches_oracle_exactly(bins, B, d, policy, load):
     for k in ("inserts_ok", "inserts_failed", "bins_viewed", "kicks", "chain_max", "ghost_pairs_made",
               "dup_evictions", "size", "live_ghosts"):
         assert s[k] == os_[k], k
-    check_table(slots, meta, bins, B, d)
+    assert s["bins_viewed_all"] == s["bins_viewed"] and s["aborts"] == 0
+    check_table(slots, meta, bins, B, d, family)
 
 
 CONCURRENT_CASES = (
     [(1 << 16, 4, 2, p, 0.95) for p in TWO_CHOICE]
     + [(1 << 15, 8, 2, p, 0.97) for p in (ck.RANDOM, ck.QUEUE, ck.SORTED | ck.GHOST)]
-    + [(1 << 18, 1, 3, ck.RANDOM, 0.90), (1 << 16, 1, 4, ck.RATTLE, 0.96), (1 << 16, 1, 4, ck.RANDOM, 0.96)]
+    + [(1 << 18, 1, 3, ck.RANDOM, 0.90), (1 << 16, 1, 4, ck.RATTLE, 0.96), (1 << 16, 1, 4, ck.RANDOM, 0.96),
+       (1 << 18, 1, 3, ck.RATTLE | 0x10000, 0.90)]
 )
 
 
@@ -100,12 +116,11 @@ CONCURRENT_CASES = (
                          ids=["%dx%d-d%d-%s-%.2f" % (b, s, d, pname(p), l) for b, s, d, p, l in CONCURRENT_CASES])
 def test_concurrent_set_semantics_match_oracle(bins, B, d, policy, load):
     keys, vals, nxt = fill_case(bins, B, d, load, 3)
-    cap = 4000 if (d > 2 and policy == ck.RANDOM) else 500
-    ref = oracle.OracleTable(bins, B, d, policy, rng_seed=7, cap=min(cap, 10 ** 6))
+    cap = 4000 if (d > 2 and policy & 0xFF == ck.RANDOM) else 500
+    ref, t, family = make_pair(bins, B, d, policy, 7, cap)
+    policy &= 0xFFFF
     ost = ref.insert(keys, vals)
     assert (ost == 0).all()
-    t = ck.CuckooTable(bins, B, d, policy, seed=7)
-    t.set_param(ck.PARAM_CHAIN_CAP, cap)
     kt, vt = ck.as_u32_tensor(keys), ck.as_u32_tensor(vals)
     # batches of 1/64 of the slots, the ratio of 2^20-key batches to a 2^26-slot
     # table, plus a ragged tail
@@ -116,13 +131,15 @@ def test_concurrent_set_semantics_match_oracle(bins, B, d, policy, load):
     st = torch.cat(sts).cpu().numpy()
     assert (st == 0).all(), np.bincount(st)
     slots, meta = t.export()
-    info = check_table(slots, meta, bins, B, d)
+    info = check_table(slots, meta, bins, B, d, family)
     assert info["size"] == len(keys)
     assert t.contents() == ref.contents()
     s, os_ = t.stats(), ref.stats()
     assert s["size"] == len(keys) and s["live_ghosts"] == info["ghost_pairs"]
-    # bins viewed per insertion: within 10% of the serial oracle at the same load
+    # bins viewed per insertion (the applied attempts): within 10% of the serial
+    # oracle at the same load
     assert abs(s["bins_viewed"] / os_["bins_viewed"] - 1) < 0.10, (s["bins_viewed"], os_["bins_viewed"])
+    assert s["bins_viewed_all"] >= s["bins_viewed"]
     # lookups, 50% present / 50% absent
     probe, expect = inputs.lookup_keys(keys, 1 << 16, 9, 0.5, next_start=nxt)
     v, fnd = t.lookup(ck.as_u32_tensor(probe))
@@ -135,7 +152,7 @@ def test_concurrent_set_semantics_match_oracle(bins, B, d, policy, load):
     assert np.array_equal(fd, ref.delete(dk))
     assert t.contents() == ref.contents()
     slots, meta = t.export()
-    assert check_table(slots, meta, bins, B, d)["size"] == ref.stats()["size"]
+    assert check_table(slots, meta, bins, B, d, family)["size"] == ref.stats()["size"]
     # re-insert half of the deleted keys after the deletes
     back = dk[: len(keys) // 16]
     st2 = t.insert(ck.as_u32_tensor(back), ck.as_u32_tensor(inputs.values_for(back))).cpu().numpy()

@@ -71,3 +71,23 @@ def test_first_bin_is_fmix_of_key_xor_seed_mod_n():
     t = oracle.OracleTable(n, 4, 2, oracle.RANDOM)
     assert t.bins_of(0x9E3779B9 ^ 1)[0] == 0x514E28B7 % n
     assert t.bins_of(0x9E3779B9)[0] == 0
+
+
+def test_xor_seeded_family_swaps_bins_decorrelated_does_not():
+    """Hash family 0, fmix32(k ^ seed_i), maps k' = k ^ seed_0 ^ seed_1 to
+    k's first two bins swapped (an algebraic fact: k' ^ seed_0 = k ^ seed_1);
+    family 1 breaks that structure."""
+    n = 1 << 20
+    t0 = oracle.OracleTable(n, 1, 3, oracle.RANDOM)
+    t1 = oracle.OracleTable(n, 1, 3, oracle.RANDOM)
+    t1.set_hash_family(1)
+    keys, _ = inputs.distinct_keys(300, 77)
+    swapped = 0
+    for k in keys:
+        k2 = int(k) ^ 0x9E3779B9 ^ 0x85EBCA6B
+        a, b = t0.bins_of(int(k)), t0.bins_of(k2)
+        if a[0] != a[1] and b[0] != b[1]:
+            assert (b[0], b[1]) == (a[1], a[0])
+        a1, b1 = t1.bins_of(int(k)), t1.bins_of(k2)
+        swapped += (b1[0], b1[1]) == (a1[1], a1[0])
+    assert swapped == 0

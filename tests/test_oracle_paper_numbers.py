@@ -151,3 +151,22 @@ def test_curves_scale_with_table_size():
     small = curve(oracle.QUEUE, trials=4, lo=0.93, hi=0.95, nb=1 << 11)[0]
     large = curve(oracle.QUEUE, trials=1, lo=0.93, hi=0.95, nb=1 << 15)[0]
     assert abs(small / large - 1) < 0.15
+
+
+@pytest.mark.slow
+def test_rattle_d3_needs_independent_hashes():
+    """Reading of Sec. 3 ("uniformly randomly generated hashes"): with the
+    XOR-seeded family the d hash functions are not independent and 3-ary
+    rattle-kicking at 90% fails keys in large tables; the decorrelated family
+    behaves like independent hashes and fails (almost) none."""
+    nb = 1 << 23
+    n = inputs.load_target(nb, 0.90)
+    keys, _ = inputs.distinct_keys(n, 2)
+    vals = inputs.values_for(keys)
+    fails = []
+    for family in (0, 1):
+        t = oracle.OracleTable(nb, 1, 3, oracle.RATTLE, rng_seed=1, cap=500)
+        t.set_hash_family(family)
+        fails.append(int((t.insert(keys, vals) != 0).sum()))
+        t.close()
+    assert fails[0] >= 10 and fails[1] <= 2, fails
