@@ -81,7 +81,7 @@ def workload(seed: int):
 class Clocks:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,clocks.mem")
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
@@ -108,7 +108,7 @@ class Clocks:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, smax, reasons = [], 0.0, set()
+        sm, smax, mem, reasons = [], 0.0, [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
@@ -117,6 +117,8 @@ class Clocks:
             try:
                 sm.append(float(parts[1]))
                 smax = max(smax, float(parts[2]))
+                if len(parts) > 9:
+                    mem.append(float(parts[9]))
             except ValueError:
                 continue
             for name, flag in zip(names, parts[5:9]):
@@ -124,8 +126,11 @@ class Clocks:
                     reasons.add(name)
         if not sm:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+               "samples": len(sm)}
+        if mem:
+            out["mem_mhz"] = statistics.median(mem)
+        return out
 
 
 # ---------------------------------------------------------------------------
@@ -224,16 +229,23 @@ def policy_fills(torch, ck, stream, base_keys):
             ("random_d3_0.90", 1 << 26, 1, 3, ck.RANDOM, 0.90, 4096),
             ("rattle_d3_0.90", 1 << 26, 1, 3, ck.RATTLE, 0.90, 500),
             ("random_d4_0.96", 1 << 26, 1, 4, ck.RANDOM, 0.96, 4096),
-            ("rattle_d4_0.96", 1 << 26, 1, 4, ck.RATTLE, 0.96, 500)):
+            ("rattle_d4_0.96", 1 << 26, 1, 4, ck.RATTLE, 0.96, 500),
+            ("random_d3_0.90_hash1", 1 << 26, 1, 3, ck.RANDOM | 0x10000, 0.90, 4096),
+            ("rattle_d3_0.90_hash1", 1 << 26, 1, 3, ck.RATTLE | 0x10000, 0.90, 500),
+            ("random_d4_0.96_hash1", 1 << 26, 1, 4, ck.RANDOM | 0x10000, 0.96, 4096),
+            ("rattle_d4_0.96_hash1", 1 << 26, 1, 4, ck.RATTLE | 0x10000, 0.96, 500)):
         n = inputs.load_target(bins * b, load)
         keys, nxt = inputs.distinct_keys(n, 2)
         kt, vt = ck.as_u32_tensor(keys), ck.as_u32_tensor(inputs.values_for(keys))
         st = torch.empty(n, dtype=torch.uint8, device="cuda")
-        t = ck.CuckooTable(bins, b, d, pol, seed=1)
+        family = 1 if pol & 0x10000 else 0  # 0x10000 here: the decorrelated hash family
+        t = ck.CuckooTable(bins, b, d, pol & 0xFFFF, seed=1)
         t.set_param(ck.PARAM_CHAIN_CAP, cap)
+        t.set_param(ck.PARAM_HASH_FAMILY, family)
         ms, _ = fill_once(torch, ck, t, kt, vt, st, stream)
         s = t.stats()
         rec = {"table": "2^%dx%d d=%d" % (int(np.log2(bins)), b, d), "load": load, "cap": cap,
+               "hash_family": family,
                "m_inserts_per_s": round(n / ms / 1e3, 2),
                "bins_viewed_per_insert": round(s["bins_viewed_per_insert"], 4),
                "chain_max": s["chain_max"], "failed": s["inserts_failed"], "aborted": s["inserts_aborted"]}

@@ -26,12 +26,13 @@
 namespace ck {
 
 constexpr uint64_t EMPTY = ~0ull;
+constexpr uint32_t NO_BIN = 0xFFFFFFFFu;
 constexpr uint32_t RESERVED_KEY = 0xFFFFFFFFu;
 
 constexpr int MAX_B = 8;
 constexpr int MAX_CHAIN = 512;    // plan entries kept in local memory by the concurrent kernel
 constexpr int LONG_CHAIN = 4104;  // plan entries of a scratch-backed plan (walk cap <= 4096)
-constexpr int LONG_REGION = 69888;  // bytes of one scratch plan (17 * LONG_CHAIN, 256-aligned)
+constexpr int LONG_REGION = 65792;  // bytes of one scratch plan (16 * LONG_CHAIN, 256-aligned)
 constexpr int MAX_GROUPS = 512;   // bins a search can view (budget <= MAX_GROUPS)
 constexpr int VISITED_SLOTS = 1024;
 constexpr int SLAB = 256;         // search regions per slab (one slab per block, blockDim <= SLAB)
@@ -186,14 +187,20 @@ __device__ __forceinline__ void fence_release() {
 }
 
 __device__ __forceinline__ bool cas_acquire(uint32_t* p, uint32_t expected, uint32_t desired) {
-  cuda::atomic_ref<uint32_t, cuda::thread_scope_device> a(*p);
-  return a.compare_exchange_strong(expected, desired, cuda::memory_order_acquire,
-                                   cuda::memory_order_relaxed);
+  uint32_t old;
+  asm volatile("atom.acquire.gpu.global.cas.b32 %0, [%1], %2, %3;"
+               : "=r"(old) : "l"(p), "r"(expected), "r"(desired) : "memory");
+  return old == expected;
 }
 
 __device__ __forceinline__ uint32_t add_release(uint32_t* p, uint32_t delta) {
   cuda::atomic_ref<uint32_t, cuda::thread_scope_device> a(*p);
   return a.fetch_add(delta, cuda::memory_order_release);
+}
+
+// Fire-and-forget atomic add (no value returned).
+__device__ __forceinline__ void red_relaxed(uint32_t* p, uint32_t delta) {
+  asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" :: "l"(p), "r"(delta) : "memory");
 }
 
 __device__ __forceinline__ uint32_t add_relaxed(uint32_t* p, uint32_t delta) {
@@ -218,6 +225,16 @@ __device__ __forceinline__ void load_view(const DevTable& t, uint32_t bin, View<
 #pragma unroll
     for (int q = 0; q < B; q += 4) ld_bin4(p + q, v.s + q);
   }
+}
+
+// Slot s of a view, s known only at run time: a chain of selects keeps the
+// view in registers (indexing the array would move it to local memory).
+template <int B>
+__device__ __forceinline__ uint64_t slot_of(const View<B>& v, int s) {
+  uint64_t r = v.s[0];
+#pragma unroll
+  for (int q = 1; q < B; q++) r = (s == q) ? v.s[q] : r;
+  return r;
 }
 
 // slot predicates on a view (claim bits cover every in-flight writer)

@@ -24,46 +24,55 @@ namespace ck {
 
 enum Kind : uint8_t { K_MOVE = 0, K_DUPTERM = 1, K_TWIN = 2, K_GHOST = 3 };
 
-// A plan: parallel arrays of claimed slots.  The arrays live in local
-// memory (MAX_CHAIN entries, the concurrent kernel) or in table scratch
-// (LONG_CHAIN entries, the serial replay and the pass for long chains).
+// A plan: one 16-byte entry per claimed slot, stored as two 64-bit words:
+// a packed descriptor -- bits 0-31 bin, 32-34 slot, 35-36 kind, 37
+// hit-counter increment, 40-47 rattle counter of the displaced key, 48-55
+// rattle counter of the incoming key -- and the record the slot held when it
+// was claimed.  Entries live in local memory (MAX_CHAIN of them, the
+// concurrent kernel) or in table scratch (LONG_CHAIN: the serial replay and
+// chains longer than MAX_CHAIN).
 struct Plan {
-  uint64_t* content;  // record the slot held when claimed (EMPTY for a free slot)
-  uint32_t* bin;
-  uint8_t* slot;
-  uint8_t* kind;
-  uint8_t* hit;       // the claim also advanced the hit counter
-  uint8_t* old_r;     // d-ary: rattle counter stored with the displaced key
-  uint8_t* new_r;     // d-ary: rattle counter stored with the incoming key
+  uint64_t* e;  // 2 * cap words
   int n;
-  int cap;            // entries the arrays hold
+  int cap;
 };
 
 template <int N>
 struct PlanStore {
-  uint64_t content[N];
-  uint32_t bin[N];
-  uint8_t slot[N], kind[N], hit[N], old_r[N], new_r[N];
+  alignas(16) uint64_t e[2 * N];  // entries are stored as 16-byte vectors
   __device__ __forceinline__ Plan view() {
-    Plan p{content, bin, slot, kind, hit, old_r, new_r, 0, N};
+    Plan p{e, 0, N};
     return p;
   }
 };
 
-// Plan arrays carved from a scratch region of LONG_REGION bytes.
 __device__ __forceinline__ Plan plan_in(uint8_t* r) {
-  Plan p;
-  p.content = reinterpret_cast<uint64_t*>(r);
-  p.bin = reinterpret_cast<uint32_t*>(r + 8 * LONG_CHAIN);
-  p.slot = r + 12 * LONG_CHAIN;
-  p.kind = r + 13 * LONG_CHAIN;
-  p.hit = r + 14 * LONG_CHAIN;
-  p.old_r = r + 15 * LONG_CHAIN;
-  p.new_r = r + 16 * LONG_CHAIN;
-  p.n = 0;
-  p.cap = LONG_CHAIN;
+  Plan p{reinterpret_cast<uint64_t*>(r), 0, LONG_CHAIN};
   return p;
 }
+
+// p.e is 16-byte aligned: a PlanStore array or a 256-byte aligned scratch region.
+__device__ __forceinline__ void put_entry(Plan& p, uint64_t desc, uint64_t content) {
+  ulonglong2 v;
+  v.x = desc;
+  v.y = content;
+  *reinterpret_cast<ulonglong2*>(p.e + 2 * p.n) = v;
+  p.n++;
+}
+__device__ __forceinline__ uint64_t desc_at(const Plan& p, int i) { return p.e[2 * i]; }
+__device__ __forceinline__ uint64_t content_at(const Plan& p, int i) { return p.e[2 * i + 1]; }
+
+__device__ __forceinline__ uint64_t pack_entry(uint32_t bin, int slot, int kind, bool hit, uint32_t old_r,
+                                               uint32_t new_r) {
+  return (uint64_t)bin | ((uint64_t)slot << 32) | ((uint64_t)kind << 35) | ((uint64_t)(hit ? 1 : 0) << 37) |
+         ((uint64_t)(old_r & 255u) << 40) | ((uint64_t)(new_r & 255u) << 48);
+}
+__device__ __forceinline__ uint32_t e_bin(uint64_t e) { return (uint32_t)e; }
+__device__ __forceinline__ uint32_t e_slot(uint64_t e) { return (uint32_t)(e >> 32) & 7u; }
+__device__ __forceinline__ uint32_t e_kind(uint64_t e) { return (uint32_t)(e >> 35) & 3u; }
+__device__ __forceinline__ bool e_hit(uint64_t e) { return (e >> 37) & 1u; }
+__device__ __forceinline__ uint32_t e_old_r(uint64_t e) { return (uint32_t)(e >> 40) & 255u; }
+__device__ __forceinline__ uint32_t e_new_r(uint64_t e) { return (uint32_t)(e >> 48) & 255u; }
 
 struct Ctx {
   uint32_t key;
@@ -78,59 +87,109 @@ struct Ctx {
   uint32_t ghosts_made;
   uint32_t dup_evict;
   Plan* plan;
+  Plan lp;      // scratch plan, once the local one is outgrown
+  int long_id;  // its index in the table's pool, or -1
+  uint64_t held;  // d-ary walks: the record in hand
 };
 
-// Claim slot s of `bin` by CAS from the viewed metadata word m (extra: the
-// hit-counter increment of queue-kicking) and append the entry.
-__device__ __forceinline__ bool claim(const DevTable& t, Ctx& c, uint32_t bin, uint32_t m, int s,
-                                      uint64_t content, uint8_t kind, bool hit,
-                                      uint8_t old_r = 0, uint8_t new_r = 0) {
+// Scratch plans for chains longer than a thread's local plan: a pool with a
+// busy flag per plan.  Taking one never waits unboundedly: after a bounded
+// number of sweeps it gives up (the attempt is then retried).
+__device__ __forceinline__ int acquire_long(const DevTable& t, uint32_t key) {
+  for (uint32_t round = 0; round < 256; round++) {
+    uint32_t start = fmix32(key + round) % t.n_long;
+    for (uint32_t k = 0; k < t.n_long; k++) {
+      uint32_t r = start + k;
+      if (r >= t.n_long) r -= t.n_long;
+      if (*(volatile uint32_t*)(t.long_busy + r) == 0 && atomicCAS(t.long_busy + r, 0u, 1u) == 0u) return (int)r;
+    }
+    __nanosleep(1000);
+  }
+  return -1;
+}
+
+__device__ __forceinline__ void release_long(const DevTable& t, int r) {
+  __threadfence();
+  atomicExch(t.long_busy + r, 0u);
+}
+
+// The local plan is full: copy the chain into a scratch plan and go on.
+__device__ __forceinline__ bool grow_plan(const DevTable& t, Ctx& c) {
+  if (c.long_id >= 0) return false;
+  int id = acquire_long(t, c.key);
+  if (id < 0) return false;
+  Plan lp = plan_in(t.long_scratch + (uint64_t)id * LONG_REGION);
+  for (int i = 0; i < 2 * c.plan->n; i++) lp.e[i] = c.plan->e[i];
+  lp.n = c.plan->n;
+  c.lp = lp;
+  c.plan = &c.lp;
+  c.long_id = id;
+  return true;
+}
+
+// Room for the next few entries: 0, or the status to give up with (a full
+// scratch plan cannot happen under the cap; no free scratch plan: retry).
+__device__ __forceinline__ int plan_room(const DevTable& t, Ctx& c) {
+  if (c.plan->n < c.plan->cap - 4) return 0;
+  if (grow_plan(t, c)) return 0;
+  return c.long_id >= 0 ? (int)ST_FAILED : (int)ST_CONFLICT;
+}
+
+// Claim slot s of `bin` by CAS from the viewed metadata word m (hit: the
+// claim also advances queue-kicking's hit counter) and append the entry.
+__device__ __forceinline__ bool claim(const DevTable& t, Ctx& c, uint32_t bin, uint32_t m, int s, uint8_t kind,
+                                      bool hit, uint64_t content, uint32_t old_r = 0, uint32_t new_r = 0) {
   uint32_t desired = m + (hit ? HIT_ONE : 0u) + (1u << s);
   if (!cas_acquire(t.meta + bin, m, desired)) return false;
-  Plan& p = *c.plan;
-  int i = p.n++;
-  p.content[i] = content;
-  p.bin[i] = bin;
-  p.slot[i] = (uint8_t)s;
-  p.kind[i] = kind;
-  p.hit[i] = hit ? 1 : 0;
-  p.old_r[i] = old_r;
-  p.new_r[i] = new_r;
+  put_entry(*c.plan, pack_entry(bin, s, kind, hit, old_r, new_r), content);
   return true;
 }
 
 // Abandon the plan: drop every claim (and hit increment); nothing was written.
 __device__ __forceinline__ void release_all(const DevTable& t, Ctx& c) {
   Plan& p = *c.plan;
-  for (int i = 0; i < p.n; i++)
-    add_relaxed(t.meta + p.bin[i], 0u - ((1u << p.slot[i]) + (p.hit[i] ? HIT_ONE : 0u)));
+  for (int i = 0; i < p.n; i++) {
+    uint64_t e = desc_at(p, i);
+    red_relaxed(t.meta + e_bin(e), 0u - ((1u << e_slot(e)) + (e_hit(e) ? HIT_ONE : 0u)));
+  }
   p.n = 0;
 }
 
-// Apply the plan back to front, then release every claim with one atomic
-// per slot that also moves the version, duplicate mark and rattle counter.
+// Apply the plan back to front, then release every claim.  Entry 0 of the
+// chain receives the new record, entry i the record entry i-1 held.  With
+// ordered writes a release fence separates consecutive stores, so a key is
+// never absent for a concurrent reader (Sec. 8); one fence then orders all
+// stores before the relaxed releases, each of which also moves the version,
+// duplicate mark or rattle counter of its slot.
 template <int B>
 __device__ __forceinline__ void commit(const DevTable& t, Ctx& c) {
   Plan& p = *c.plan;
   int n_chain = 0;
-  while (n_chain < p.n && (p.kind[n_chain] == K_MOVE || p.kind[n_chain] == K_DUPTERM)) n_chain++;
+  while (n_chain < p.n && (e_kind(desc_at(p, n_chain)) == K_MOVE || e_kind(desc_at(p, n_chain)) == K_DUPTERM))
+    n_chain++;
   for (int i = n_chain - 1; i >= 0; i--) {
-    uint64_t rec = (i == 0) ? c.krec : p.content[i - 1];
-    st_slot(t.slots + (uint64_t)p.bin[i] * B + p.slot[i], rec);
+    uint64_t rec = (i == 0) ? c.krec : content_at(p, i - 1);
+    uint64_t ei = desc_at(p, i);
+    st_slot(t.slots + (uint64_t)e_bin(ei) * B + e_slot(ei), rec);
     if (t.ordered_writes && i > 0) fence_release();  // the copy lands before its source is overwritten
   }
-  for (int i = n_chain; i < p.n; i++)
-    if (p.kind[i] == K_GHOST) st_slot(t.slots + (uint64_t)p.bin[i] * B + p.slot[i], c.krec);
+  for (int i = n_chain; i < p.n; i++) {
+    uint64_t ei = desc_at(p, i);
+    if (e_kind(ei) == K_GHOST) st_slot(t.slots + (uint64_t)e_bin(ei) * B + e_slot(ei), c.krec);
+  }
+  fence_release();
   for (int i = 0; i < p.n; i++) {
-    uint32_t delta = VER_ONE - (1u << p.slot[i]);
+    uint64_t ei = desc_at(p, i);
+    uint32_t sl = e_slot(ei);
+    uint32_t delta = VER_ONE - (1u << sl);
     if (B == 1) {
-      delta += ((uint32_t)p.new_r[i] - (uint32_t)p.old_r[i]) << RATTLE_SHIFT;
-    } else if (p.kind[i] == K_GHOST) {
-      delta += 1u << (DUP_SHIFT + p.slot[i]);
-    } else if (p.kind[i] == K_DUPTERM || p.kind[i] == K_TWIN) {
-      delta -= 1u << (DUP_SHIFT + p.slot[i]);
+      delta += (e_new_r(ei) - e_old_r(ei)) << RATTLE_SHIFT;
+    } else if (e_kind(ei) == K_GHOST) {
+      delta += 1u << (DUP_SHIFT + sl);
+    } else if (e_kind(ei) == K_DUPTERM || e_kind(ei) == K_TWIN) {
+      delta -= 1u << (DUP_SHIFT + sl);
     }
-    add_release(t.meta + p.bin[i], delta);
+    red_relaxed(t.meta + e_bin(ei), delta);
   }
 }
 
@@ -140,7 +199,7 @@ __device__ __forceinline__ bool claims_none_foreign(const Ctx& c) { return !c.fo
 
 __device__ __forceinline__ bool plan_has_bin(const Plan& p, uint32_t bin) {
   for (int i = 0; i < p.n; i++)
-    if (p.bin[i] == bin) return true;
+    if (e_bin(desc_at(p, i)) == bin) return true;
   return false;
 }
 
@@ -149,7 +208,7 @@ template <int B>
 __device__ __forceinline__ bool claims_all_ours(const Plan& p, uint32_t bin, uint32_t claimed) {
   uint32_t ours = 0;
   for (int i = 0; i < p.n; i++)
-    if (p.bin[i] == bin) ours |= 1u << p.slot[i];
+    if (e_bin(desc_at(p, i)) == bin) ours |= 1u << e_slot(desc_at(p, i));
   return (claimed & ~ours) == 0;
 }
 
@@ -167,7 +226,7 @@ __device__ __forceinline__ bool claim_twin(const DevTable& t, Ctx& c, uint64_t g
     for (int u = 0; u < B; u++)
       if (s < 0 && ((dm >> u) & 1u) && v.s[u] == g) s = u;
     if (s < 0) return false;
-    if (claim(t, c, y, v.m, s, g, K_TWIN, false)) return true;
+    if (claim(t, c, y, v.m, s, K_TWIN, false, g)) return true;
   }
   return false;
 }
@@ -182,7 +241,7 @@ template <int B>
 __device__ __forceinline__ int take_free(const DevTable& t, Ctx& c, uint32_t bin, View<B>& v, int s,
                                          bool hit) {
   for (int tries = 0;; tries++) {
-    if (claim(t, c, bin, v.m, s, EMPTY, K_MOVE, hit)) return ST_OK;
+    if (claim(t, c, bin, v.m, s, K_MOVE, hit, EMPTY)) return ST_OK;
     if (tries == 3) return ST_CONFLICT;
     load_view<B>(t, bin, v);
     c.viewed++;
@@ -197,24 +256,20 @@ __device__ __forceinline__ int take_free(const DevTable& t, Ctx& c, uint32_t bin
 template <int B>
 __device__ __forceinline__ int take_dup(const DevTable& t, Ctx& c, uint32_t bin, View<B>& v, int s,
                                         bool hit) {
-  uint64_t g = v.s[s];
+  uint64_t g = slot_of<B>(v, s);
   uint32_t y = other_bin2(t, g, bin);
   if (y < bin) {
     if (!claim_twin<B>(t, c, g, y)) return ST_CONFLICT;
-    if (!claim(t, c, bin, v.m, s, g, K_DUPTERM, hit)) return ST_CONFLICT;
+    if (!claim(t, c, bin, v.m, s, K_DUPTERM, hit, g)) return ST_CONFLICT;
     // keep the chain entries contiguous: the twin goes after the terminal
     Plan& p = *c.plan;
-    int a = p.n - 2, b = p.n - 1;
-    uint64_t tc = p.content[a]; p.content[a] = p.content[b]; p.content[b] = tc;
-    uint32_t tb = p.bin[a]; p.bin[a] = p.bin[b]; p.bin[b] = tb;
-    uint8_t t8;
-    t8 = p.slot[a]; p.slot[a] = p.slot[b]; p.slot[b] = t8;
-    t8 = p.kind[a]; p.kind[a] = p.kind[b]; p.kind[b] = t8;
-    t8 = p.hit[a]; p.hit[a] = p.hit[b]; p.hit[b] = t8;
-    t8 = p.old_r[a]; p.old_r[a] = p.old_r[b]; p.old_r[b] = t8;
-    t8 = p.new_r[a]; p.new_r[a] = p.new_r[b]; p.new_r[b] = t8;
+    uint64_t td = p.e[2 * (p.n - 2)], tc = p.e[2 * (p.n - 2) + 1];
+    p.e[2 * (p.n - 2)] = p.e[2 * (p.n - 1)];
+    p.e[2 * (p.n - 2) + 1] = p.e[2 * (p.n - 1) + 1];
+    p.e[2 * (p.n - 1)] = td;
+    p.e[2 * (p.n - 1) + 1] = tc;
   } else {
-    if (!claim(t, c, bin, v.m, s, g, K_DUPTERM, hit)) return ST_CONFLICT;
+    if (!claim(t, c, bin, v.m, s, K_DUPTERM, hit, g)) return ST_CONFLICT;
     if (!claim_twin<B>(t, c, g, y)) return ST_CONFLICT;
   }
   c.dup_evict++;
@@ -227,13 +282,13 @@ template <int B>
 __device__ __forceinline__ int take_victim(const DevTable& t, Ctx& c, uint32_t bin, View<B>& v, int s,
                                            bool hit) {
   for (int tries = 0;; tries++) {
-    if (claim(t, c, bin, v.m, s, v.s[s], K_MOVE, hit)) return ST_OK;
+    if (claim(t, c, bin, v.m, s, K_MOVE, hit, slot_of<B>(v, s))) return ST_OK;
     if (tries == 3) return ST_CONFLICT;
     load_view<B>(t, bin, v);
     c.viewed++;
     c.reviews++;
     uint32_t usable = ~claimed_mask<B>(v) & ~(v.m >> DUP_SHIFT);
-    if (((usable >> s) & 1u) == 0 || v.s[s] == EMPTY) return ST_CONFLICT;
+    if (((usable >> s) & 1u) == 0 || slot_of<B>(v, s) == EMPTY) return ST_CONFLICT;
   }
 }
 
@@ -261,8 +316,8 @@ __device__ int insert_random2(const DevTable& t, Ctx& c) {
     c.viewed += 2;
     uint32_t f0 = free_mask<B>(v0), f1 = free_mask<B>(v1);
     if (f0 && f1) {
-      if (!claim(t, c, b0, v0.m, lowest(f0), EMPTY, K_GHOST, false)) return ST_CONFLICT;
-      if (!claim(t, c, b1, v1.m, lowest(f1), EMPTY, K_GHOST, false)) return ST_CONFLICT;
+      if (!claim(t, c, b0, v0.m, lowest(f0), K_GHOST, false, EMPTY)) return ST_CONFLICT;
+      if (!claim(t, c, b1, v1.m, lowest(f1), K_GHOST, false, EMPTY)) return ST_CONFLICT;
       c.ghosts_made++;
       return ST_OK;
     }
@@ -288,7 +343,7 @@ __device__ int insert_random2(const DevTable& t, Ctx& c) {
     int st = take_victim<B>(t, c, x, vx, s, false);
     if (st != ST_OK) return st;
     c.kicks++;
-    uint64_t victim = vx.s[s];
+    uint64_t victim = slot_of<B>(vx, s);
     x = other_bin2(t, victim, x);
     load_view<B>(t, x, vx);
     c.viewed++;
@@ -301,7 +356,7 @@ __device__ int insert_random2(const DevTable& t, Ctx& c) {
     uint32_t claimed = claimed_mask<B>(vx);
     uint32_t e = FULL & ~claimed & ~(vx.m >> DUP_SHIFT);
     if (!e) return claims_all_ours<B>(*c.plan, x, claimed) ? ST_FAILED : ST_CONFLICT;
-    if (c.plan->n >= c.plan->cap - 4) return ST_LONG;
+    if (int r0 = plan_room(t, c)) return r0;
     uint64_t r = draw(t, c.key, c.draws++, c.attempt);
     s = nth_bit(e, (uint32_t)(r % __popc(e)));
   }
@@ -327,8 +382,8 @@ __device__ int insert_queue(const DevTable& t, Ctx& c) {
   if (GHOST && f0 > 0 && f1 > 0) {
     int s0 = first_from<B>(fm0, hit_of(v0.m) % B);
     int s1 = first_from<B>(fm1, hit_of(v1.m) % B);
-    if (!claim(t, c, b0, v0.m, s0, EMPTY, K_GHOST, true)) return ST_CONFLICT;
-    if (!claim(t, c, b1, v1.m, s1, EMPTY, K_GHOST, true)) return ST_CONFLICT;
+    if (!claim(t, c, b0, v0.m, s0, K_GHOST, true, EMPTY)) return ST_CONFLICT;
+    if (!claim(t, c, b1, v1.m, s1, K_GHOST, true, EMPTY)) return ST_CONFLICT;
     c.ghosts_made++;
     return ST_OK;
   }
@@ -353,7 +408,7 @@ __device__ int insert_queue(const DevTable& t, Ctx& c) {
       uint32_t h = hit_of(vx.m) % B;
       uint32_t fm = free_mask<B>(vx);
       if (fm) {
-        if (claim(t, c, x, vx.m, first_from<B>(fm, h), EMPTY, K_MOVE, true)) return ST_OK;
+        if (claim(t, c, x, vx.m, first_from<B>(fm, h), K_MOVE, true, EMPTY)) return ST_OK;
       } else if (GHOST && dup_mask<B>(vx)) {
         return take_dup<B>(t, c, x, vx, first_from<B>(dup_mask<B>(vx), h), true);
       } else {
@@ -362,10 +417,10 @@ __device__ int insert_queue(const DevTable& t, Ctx& c) {
         int s = first_from<B>(um, h);
         if (s < 0) return claims_all_ours<B>(*c.plan, x, claimed) ? ST_FAILED : ST_CONFLICT;
         if (c.kicks == t.cap) return ST_FAILED;
-        if (c.plan->n >= c.plan->cap - 4) return ST_LONG;
-        if (claim(t, c, x, vx.m, s, vx.s[s], K_MOVE, true)) {
+        if (int r0 = plan_room(t, c)) return r0;
+        if (claim(t, c, x, vx.m, s, K_MOVE, true, slot_of<B>(vx, s))) {
           c.kicks++;
-          x = other_bin2(t, vx.s[s], x);
+          x = other_bin2(t, slot_of<B>(vx, s), x);
           break;
         }
       }
@@ -386,7 +441,7 @@ __device__ int insert_queue(const DevTable& t, Ctx& c) {
 // Random kicking: view h_0.. in order until an empty bin; when all d are
 // full displace the occupant of a uniformly drawn h_j, which moves to a
 // uniformly drawn bin of its own that the chain has not written, and so on.
-__device__ int insert_random_dary(const DevTable& t, Ctx& c) {
+__device__ inline int insert_random_dary(const DevTable& t, Ctx& c) {
   uint32_t b[4];
   bins_of(t, c.key, b);
   View<1> v[4];
@@ -395,40 +450,87 @@ __device__ int insert_random_dary(const DevTable& t, Ctx& c) {
     if (i < (int)t.d) load_view<1>(t, b[i], v[i]);  // the d loads overlap
   for (uint32_t i = 0; i < t.d; i++) {
     c.viewed++;
-    if (free_mask<1>(v[i])) return take_free<1>(t, c, b[i], v[i], 0, false);
+    if (free_mask<1>(v[i]) && take_free<1>(t, c, b[i], v[i], 0, false) == ST_OK) return ST_OK;
   }
-  // all d full: a uniform unclaimed h_j (claimed bins are ignored, Sec. 8)
-  uint32_t elig[4], ne = 0;
-  for (uint32_t i = 0; i < t.d; i++)
-    if (!claimed_mask<1>(v[i])) elig[ne++] = i;
-  if (ne == 0) return ST_CONFLICT;
-  uint32_t j = elig[draw(t, c.key, c.draws++, c.attempt) % ne];
-  uint32_t x = b[j];
-  View<1> vx = v[j];
-  for (;;) {
-    if (c.kicks == t.cap) return ST_FAILED;
-    if (c.plan->n >= c.plan->cap - 4) return ST_LONG;
-    int st = take_victim<1>(t, c, x, vx, 0, false);
-    if (st != ST_OK) return st;
-    c.kicks++;
-    uint64_t victim = vx.s[0];
-    uint32_t vb[4], cand[4], nc = 0;
-    bins_of(t, key_of(victim), vb);
-    for (uint32_t i = 0; i < t.d; i++)
-      if (!plan_has_bin(*c.plan, vb[i])) cand[nc++] = vb[i];
-    // a uniform bin of the victim's own that this chain has not written;
-    // one another insertion holds is dropped and the draw repeated
-    for (;;) {
-      if (nc == 0) return claims_none_foreign(c) ? ST_FAILED : ST_CONFLICT;
-      uint32_t k = (uint32_t)(draw(t, c.key, c.draws++, c.attempt) % nc);
-      x = cand[k];
-      load_view<1>(t, x, vx);
-      c.viewed++;
-      if (!claimed_mask<1>(vx)) break;
-      c.foreign = 1;
-      cand[k] = cand[--nc];
+  // Every bin of the record in hand is full: displace the occupant of a
+  // uniformly drawn candidate -- one of the record's bins whose claim flag
+  // is clear.  With one insertion in flight the set claims are exactly this
+  // chain's own, so these are the bins the chain has not written.  The
+  // candidates' slots are fetched together; only the drawn one counts as
+  // viewed.  A candidate another insertion took meanwhile is dropped and the
+  // draw repeated.
+  uint32_t cb[4], nc = 0;
+  View<1> cv[4];
+  for (uint32_t i = 0; i < t.d; i++) {
+    if (!claimed_mask<1>(v[i])) { cb[nc] = b[i]; cv[nc] = v[i]; nc++; }
+    else c.foreign = 1;  // no claim of ours exists before the first kick
+  }
+  bool counted = true;  // the first candidates were counted above
+  uint32_t holder = NO_BIN;  // the bin whose record is in hand (the last one claimed)
+  for (uint32_t waits = 0;;) {
+    if (nc == 0 && c.foreign && holder != NO_BIN && waits < 8) {
+      // every candidate is held by other insertions, which release their
+      // claims within microseconds: view the candidates again rather than
+      // abandon the whole walk (a bounded wait, so no deadlock)
+      __nanosleep(256u << waits);
+      waits++;
+      uint32_t vb[4];
+      bins_of(t, key_of(c.held), vb);
+      View<1> w[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+        if (i < (int)t.d && vb[i] != holder) load_view<1>(t, vb[i], w[i]);
+      for (uint32_t i = 0; i < t.d; i++) {
+        if (vb[i] == holder) continue;
+        if (!claimed_mask<1>(w[i])) { cb[nc] = vb[i]; cv[nc] = w[i]; nc++; }
+      }
+      c.reviews += nc;
+      continue;
     }
-    if (free_mask<1>(vx)) return take_free<1>(t, c, x, vx, 0, false);
+    if (nc == 0) return c.foreign ? ST_CONFLICT : ST_FAILED;
+    uint32_t k = (uint32_t)(draw(t, c.key, c.draws++, c.attempt) % nc);
+    uint32_t x = cb[k];
+    View<1> vx = cv[k];
+    if (!counted) c.viewed++;
+    bool kicked = false, lost = false;
+    for (int tries = 0; tries < 4 && !kicked && !lost; tries++) {
+      if (tries) {  // lost a race for x: view it again
+        load_view<1>(t, x, vx);
+        c.viewed++;
+        c.reviews++;
+      }
+      if (claimed_mask<1>(vx)) { lost = true; break; }
+      if (vx.s[0] == EMPTY) {
+        if (claim(t, c, x, vx.m, 0, K_MOVE, false, EMPTY)) return ST_OK;
+        continue;
+      }
+      if (c.kicks == t.cap) return ST_FAILED;
+      if (int r = plan_room(t, c)) return r;
+      kicked = claim(t, c, x, vx.m, 0, K_MOVE, false, vx.s[0]);
+    }
+    if (!kicked) {
+      c.foreign = 1;
+      cb[k] = cb[nc - 1];
+      cv[k] = cv[nc - 1];
+      nc--;
+      continue;
+    }
+    c.kicks++;
+    holder = x;
+    c.held = vx.s[0];
+    uint32_t vb[4];
+    bins_of(t, key_of(vx.s[0]), vb);
+    View<1> w[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+      if (i < (int)t.d && vb[i] != x) load_view<1>(t, vb[i], w[i]);
+    nc = 0;
+    for (uint32_t i = 0; i < t.d; i++) {
+      if (vb[i] == x) continue;  // just claimed by this chain
+      if (!claimed_mask<1>(w[i])) { cb[nc] = vb[i]; cv[nc] = w[i]; nc++; }
+      else if (!plan_has_bin(*c.plan, vb[i])) c.foreign = 1;
+    }
+    counted = false;
   }
 }
 
@@ -437,19 +539,27 @@ __device__ int insert_random_dary(const DevTable& t, Ctx& c) {
 // the larger counter keeps the bin, the incoming key on a tie (or the
 // resident, under the debug reading); the loser tries its next bin.  The
 // counter of a resident key lives in its bin's metadata word.
-__device__ int insert_rattle(const DevTable& t, Ctx& c) {
+__device__ inline int insert_rattle(const DevTable& t, Ctx& c) {
   uint64_t cur = c.krec;
   uint32_t rc = 0;
   for (uint32_t tries = 0;; tries++) {
-    if (tries == t.cap) return claims_none_foreign(c) ? ST_FAILED : ST_CONFLICT;
-    if (c.plan->n >= c.plan->cap - 4) return ST_LONG;
+    if (tries == t.cap) return c.foreign ? ST_CONFLICT : ST_FAILED;
+    if (int r = plan_room(t, c)) return r;
     uint32_t vb[4];
     bins_of(t, key_of(cur), vb);
     uint32_t x = vb[rc % t.d];
     rc = rc < 255 ? rc + 1 : 255;
-    if (plan_has_bin(*c.plan, x)) continue;
     View<1> vx;
     load_view<1>(t, x, vx);
+    if (claimed_mask<1>(vx)) {
+      // this chain's own bin: skipped, not viewed; another insertion's:
+      // viewed and ignored (Sec. 8)
+      if (!plan_has_bin(*c.plan, x)) {
+        c.viewed++;
+        c.foreign = 1;
+      }
+      continue;
+    }
     c.viewed++;
     bool moved = false, skip = false;
     for (int k = 0; k < 4 && !moved && !skip; k++) {
@@ -457,20 +567,20 @@ __device__ int insert_rattle(const DevTable& t, Ctx& c) {
         load_view<1>(t, x, vx);
         c.viewed++;
         c.reviews++;
-      }
-      if (claimed_mask<1>(vx)) {  // another insertion holds it: ignore the bin (Sec. 8)
-        c.foreign = 1;
-        skip = true;
-        break;
+        if (claimed_mask<1>(vx)) {
+          c.foreign = 1;
+          skip = true;
+          break;
+        }
       }
       if (vx.s[0] == EMPTY) {
-        if (claim(t, c, x, vx.m, 0, EMPTY, K_MOVE, false, (uint8_t)rattle_of(vx.m), (uint8_t)rc)) return ST_OK;
+        if (claim(t, c, x, vx.m, 0, K_MOVE, false, EMPTY, rattle_of(vx.m), rc)) return ST_OK;
         continue;
       }
       uint32_t ry = rattle_of(vx.m);
       bool incoming_stays = t.tie_resident ? (rc > ry) : (rc >= ry);
       if (!incoming_stays) { skip = true; break; }
-      if (claim(t, c, x, vx.m, 0, vx.s[0], K_MOVE, false, (uint8_t)ry, (uint8_t)rc)) {
+      if (claim(t, c, x, vx.m, 0, K_MOVE, false, vx.s[0], ry, rc)) {
         c.kicks++;
         cur = vx.s[0];
         rc = ry;

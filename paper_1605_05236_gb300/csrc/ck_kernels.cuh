@@ -33,26 +33,6 @@ __device__ __forceinline__ int attempt_insert(const DevTable& t, Ctx& c, uint8_t
   }
 }
 
-// Take a free scratch plan (for a chain longer than the local plan holds).
-// Never waits unboundedly: after a bounded number of sweeps it gives up.
-__device__ __forceinline__ int acquire_long(const DevTable& t, uint32_t key) {
-  for (uint32_t round = 0; round < 256; round++) {
-    uint32_t start = fmix32(key + round) % t.n_long;
-    for (uint32_t k = 0; k < t.n_long; k++) {
-      uint32_t r = start + k;
-      if (r >= t.n_long) r -= t.n_long;
-      if (*(volatile uint32_t*)(t.long_busy + r) == 0 && atomicCAS(t.long_busy + r, 0u, 1u) == 0u) return (int)r;
-    }
-    __nanosleep(1000);
-  }
-  return -1;
-}
-
-__device__ __forceinline__ void release_long(const DevTable& t, int r) {
-  __threadfence();
-  atomicExch(t.long_busy + r, 0u);
-}
-
 // A block's slab of search scratch: SLAB consecutive per-thread regions.
 // Taken at block start and returned at block end, so blocks of overlapping
 // launches never share a region.  A block of the next launch may wait for
@@ -74,15 +54,15 @@ __device__ __forceinline__ int acquire_slab(const DevTable& t) {
 }
 
 // One insertion with bounded retries after claim conflicts.  A chain that
-// outgrows the local plan is planned again, with the same draws, in a
-// scratch-backed plan.
+// outgrows the local plan continues in a scratch plan.  retry_failed: a
+// random walk that failed in concurrent mode is tried again with new draws
+// (up to 3 times): its path depended on the timing of other insertions.
 template <int B, int POL, bool GHOST>
 __device__ __forceinline__ int insert_one(const DevTable& t, Ctx& c, uint8_t* region, uint32_t& aborts,
-                                          Plan local) {
-  Plan lp;
-  Plan* plan = &local;
-  int long_id = -1;
+                                          Plan local, bool retry_failed = false) {
+  c.long_id = -1;
   int st;
+  uint32_t fails = 0;
   for (uint32_t attempt = 0;;) {
     c.attempt = attempt;
     c.kicks = 0;
@@ -91,28 +71,27 @@ __device__ __forceinline__ int insert_one(const DevTable& t, Ctx& c, uint8_t* re
     c.ghosts_made = 0;
     c.dup_evict = 0;
     c.foreign = 0;
-    plan->n = 0;
-    c.plan = plan;
+    c.plan = c.long_id >= 0 ? &c.lp : &local;
+    c.plan->n = 0;
     st = attempt_insert<B, POL, GHOST>(t, c, region);
     if (st == ST_OK) {
       commit<B>(t, c);
       break;
     }
     release_all(t, c);
-    if (st == ST_LONG) {
-      if (long_id >= 0) { st = ST_FAILED; break; }  // a scratch plan holds any chain under the cap
-      long_id = acquire_long(t, c.key);
-      if (long_id < 0) { st = ST_ABORTED; break; }
-      lp = plan_in(t.long_scratch + (uint64_t)long_id * LONG_REGION);
-      plan = &lp;
+    if (st == ST_LONG) {  // a search path longer than the local plan
+      if (c.long_id >= 0 || !grow_plan(t, c)) { st = c.long_id >= 0 ? ST_FAILED : ST_ABORTED; break; }
       continue;
     }
-    if (st == ST_FAILED) break;
-    aborts++;
+    if (st == ST_FAILED) {
+      if (!retry_failed || ++fails > 3) break;
+    } else {
+      aborts++;
+    }
     if (++attempt >= t.max_retries) { st = ST_ABORTED; break; }
-    backoff(attempt, c.key);
+    if (st == ST_CONFLICT) backoff(attempt, c.key);
   }
-  if (long_id >= 0) release_long(t, long_id);
+  if (c.long_id >= 0) release_long(t, c.long_id);
   return st;
 }
 
@@ -182,7 +161,8 @@ __global__ void __launch_bounds__(256) k_insert(DevTable t, const uint32_t* __re
     c.krec = ((uint64_t)key << 32) | vals[i];
     c.viewed = 0;
     c.reviews = 0;
-    int st = usable ? insert_one<B, POL, GHOST>(t, c, region, aborts, local) : (int)ST_ABORTED;
+    int st = usable ? insert_one<B, POL, GHOST>(t, c, region, aborts, local, !SERIAL && POL == P_RANDOM)
+                    : (int)ST_ABORTED;
     if (st == ST_OK) {
       ok++;
       kicks += c.kicks;
@@ -321,7 +301,7 @@ __global__ void __launch_bounds__(256) k_lookup2(DevTable t, const uint32_t* __r
 }
 
 // d-ary lookup: the d single-slot bins are fetched at once.
-__global__ void __launch_bounds__(256) k_lookup_dary(DevTable t, const uint32_t* __restrict__ keys, uint64_t n,
+static __global__ void __launch_bounds__(256) k_lookup_dary(DevTable t, const uint32_t* __restrict__ keys, uint64_t n,
                                                      uint32_t* __restrict__ vals_out,
                                                      uint8_t* __restrict__ found_out) {
   __shared__ unsigned long long hits_sh, cnt_sh;

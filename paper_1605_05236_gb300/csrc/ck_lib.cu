@@ -159,13 +159,13 @@ int init_table(ck_table* t, void* buf, size_t bytes, bool owns, uint64_t bins, u
 // ---- kernel dispatch -------------------------------------------------
 
 template <int B, int POL, bool GHOST>
-cudaError_t launch_insert(const ck_table* t, const uint32_t* keys, const uint32_t* vals, uint64_t n, uint8_t* st,
-                          uint32_t* viewed, bool serial, cudaStream_t s) {
+cudaError_t launch_insert_dt(const DevTable& dt, uint32_t block, int sm_count, bool overlap, uint64_t load_base,
+                             const uint32_t* keys, const uint32_t* vals, uint64_t n, uint8_t* st, uint32_t* viewed,
+                             bool serial, cudaStream_t s) {
   if (serial) {
-    k_insert<B, POL, GHOST, true><<<1, 1, 0, s>>>(t->dt, keys, vals, n, st, viewed, t->load_base);
+    k_insert<B, POL, GHOST, true><<<1, 1, 0, s>>>(dt, keys, vals, n, st, viewed, load_base);
     return cudaGetLastError();
   }
-  uint32_t block = t->block;
   // persistent launch: at most the blocks that fit on the GPU at once
   static int cached_block = 0, cached_per_sm = 0;
   if (cached_block != (int)block) {
@@ -178,10 +178,10 @@ cudaError_t launch_insert(const ck_table* t, const uint32_t* keys, const uint32_
     cached_block = (int)block;
   }
   uint64_t grid = (n + block - 1) / block;
-  uint64_t resident = (uint64_t)cached_per_sm * t->sm_count;
+  uint64_t resident = (uint64_t)cached_per_sm * sm_count;
   if (grid > resident) grid = resident;
-  if (t->dt.scratch) {
-    uint64_t cap_blocks = t->dt.n_searchers / SLAB;
+  if (dt.scratch) {
+    uint64_t cap_blocks = dt.n_searchers / SLAB;
     if (grid > cap_blocks) grid = cap_blocks;
   }
   if (grid > 0x7FFFFFFFull) grid = 0x7FFFFFFFull;
@@ -192,10 +192,17 @@ cudaError_t launch_insert(const ck_table* t, const uint32_t* keys, const uint32_
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = t->overlap ? 1 : 0;
+  attr[0].val.programmaticStreamSerializationAllowed = overlap ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_insert<B, POL, GHOST, false>, t->dt, keys, vals, n, st, viewed, t->load_base);
+  return cudaLaunchKernelEx(&cfg, k_insert<B, POL, GHOST, false>, dt, keys, vals, n, st, viewed, load_base);
+}
+
+template <int B, int POL, bool GHOST>
+cudaError_t launch_insert(const ck_table* t, const uint32_t* keys, const uint32_t* vals, uint64_t n, uint8_t* st,
+                          uint32_t* viewed, bool serial, cudaStream_t s) {
+  return launch_insert_dt<B, POL, GHOST>(t->dt, t->block, t->sm_count, t->overlap != 0, t->load_base, keys, vals,
+                                         n, st, viewed, serial, s);
 }
 
 using InsertFn = cudaError_t (*)(const ck_table*, const uint32_t*, const uint32_t*, uint64_t, uint8_t*,
@@ -228,6 +235,29 @@ unsigned grid_for(uint64_t n, uint32_t block) {
 }
 
 }  // namespace
+
+// Device view of a handle, for the other translation units of the library.
+const ck::DevTable* ck_internal_devtable(const ck_table* t) { return &t->dt; }
+
+// The single-table insert launch for a bare device view (the batched form's
+// one-launch-per-table reference path): concurrent mode, overlapping launches.
+int ck_internal_launch_insert(const DevTable& dt, uint32_t block, int sm_count, const uint32_t* keys,
+                              const uint32_t* vals, uint64_t n, uint8_t* status, cudaStream_t s) {
+  cudaError_t e = cudaErrorInvalidValue;
+  bool g = dt.ghost != 0;
+  if (dt.B == 4) {
+    if (dt.policy == CK_QUEUE) e = g ? launch_insert_dt<4, P_QUEUE, true>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s)
+                                     : launch_insert_dt<4, P_QUEUE, false>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s);
+    else if (dt.policy == CK_RANDOM) e = g ? launch_insert_dt<4, P_RANDOM, true>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s)
+                                           : launch_insert_dt<4, P_RANDOM, false>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s);
+  } else if (dt.B == 8) {
+    if (dt.policy == CK_QUEUE) e = g ? launch_insert_dt<8, P_QUEUE, true>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s)
+                                     : launch_insert_dt<8, P_QUEUE, false>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s);
+    else if (dt.policy == CK_RANDOM) e = g ? launch_insert_dt<8, P_RANDOM, true>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s)
+                                           : launch_insert_dt<8, P_RANDOM, false>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s);
+  }
+  return e == cudaSuccess ? CK_OK : CK_ECUDA;
+}
 
 extern "C" {
 

@@ -71,8 +71,8 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
   uint32_t f0 = free_mask<B>(v0), f1 = free_mask<B>(v1);
   if (GHOST) {
     if (f0 && f1) {
-      if (!claim(t, c, b0, v0.m, lowest(f0), EMPTY, K_GHOST, false)) return ST_CONFLICT;
-      if (!claim(t, c, b1, v1.m, lowest(f1), EMPTY, K_GHOST, false)) return ST_CONFLICT;
+      if (!claim(t, c, b0, v0.m, lowest(f0), K_GHOST, false, EMPTY)) return ST_CONFLICT;
+      if (!claim(t, c, b1, v1.m, lowest(f1), K_GHOST, false, EMPTY)) return ST_CONFLICT;
       c.ghosts_made++;
       return ST_OK;
     }
@@ -168,14 +168,12 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
     if ((int)depth + 4 > c.plan->cap) return ST_LONG;
     Plan& p = *c.plan;
     {
+      // entries in chain order; the group index rides in the content word
+      // until the slot is claimed
       uint32_t q = g, qs = s;
       for (int i = (int)depth - 1; i >= 0; i--) {
-        p.bin[i] = G[q].bin;
-        p.slot[i] = (uint8_t)qs;
-        p.kind[i] = K_MOVE;
-        p.hit[i] = 0;
-        p.old_r[i] = p.new_r[i] = 0;
-        p.content[i] = q;  // group index until the slot is claimed
+        p.e[2 * i] = pack_entry(G[q].bin, (int)qs, K_MOVE, false, 0, 0);
+        p.e[2 * i + 1] = q;
         uint32_t par = G[q].parent;
         if (par != ~0u) { qs = par & 7u; q = par >> 3; }
       }
@@ -184,11 +182,12 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
     // so the record read after the claim is the one the search saw
     p.n = 0;
     for (uint32_t i = 0; i < depth; i++) {
-      Group gq = G[(uint32_t)p.content[i]];
+      Group gq = G[(uint32_t)p.e[2 * i + 1]];
+      uint32_t sl = e_slot(p.e[2 * i]);
       if (gq.stale) return ST_CONFLICT;
-      if (!cas_acquire(t.meta + gq.bin, gq.meta, gq.meta + (1u << p.slot[i]))) return ST_CONFLICT;
+      if (!cas_acquire(t.meta + gq.bin, gq.meta, gq.meta + (1u << sl))) return ST_CONFLICT;
       p.n = (int)i + 1;
-      p.content[i] = ld_slot(t.slots + (uint64_t)gq.bin * B + p.slot[i]);
+      p.e[2 * i + 1] = ld_slot(t.slots + (uint64_t)gq.bin * B + sl);
     }
     c.kicks = depth;
     if (isdup) return take_dup<B>(t, c, y, vy, term, false);

@@ -150,3 +150,27 @@ def ref_permutation(n, seed, k=None):
         j = i + int(outs[i]) % (n - i)
         a[i], a[j] = a[j], a[i]
     return np.array(a[:k], dtype=np.int64)
+
+
+def multi_shapes(n_tables: int, seed: int = 7, lo_log2: int = 10, hi_log2: int = 18):
+    """Shapes of the batched workload: table i has floor(2^(lo + (hi-lo)*u))
+    bins, u uniform in [0,1) from output 2i of the stream of `seed` (top 53
+    bits), and 4 or 8 slots per bin from the top bit of output 2i+1."""
+    out = splitmix64_stream(seed, 0, 2 * n_tables)
+    u = (out[0::2] >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+    bins = np.floor(2.0 ** (lo_log2 + (hi_log2 - lo_log2) * u)).astype(np.uint64)
+    slots = np.where((out[1::2] >> np.uint64(63)) == 0, 4, 8).astype(np.uint32)
+    return bins, slots
+
+
+def multi_keys(bins, slots, load: float, seed0: int = 8):
+    """Per table i: floor(load * slots) distinct keys from the stream of seed
+    seed0 + i, concatenated; returns (keys, values, n_keys)."""
+    n_keys = np.array([load_target(int(b) * int(s), load) for b, s in zip(bins, slots)], dtype=np.uint64)
+    keys = np.empty(int(n_keys.sum()), dtype=np.uint32)
+    off = 0
+    for i, n in enumerate(n_keys):
+        k, _ = distinct_keys(int(n), seed0 + i)
+        keys[off:off + int(n)] = k
+        off += int(n)
+    return keys, values_for(keys), n_keys

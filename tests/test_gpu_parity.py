@@ -122,9 +122,10 @@ def test_concurrent_set_semantics_match_oracle(bins, B, d, policy, load):
     ost = ref.insert(keys, vals)
     assert (ost == 0).all()
     kt, vt = ck.as_u32_tensor(keys), ck.as_u32_tensor(vals)
-    # batches of 1/64 of the slots, the ratio of 2^20-key batches to a 2^26-slot
-    # table, plus a ragged tail
-    batch = max(1024, (bins * B) // 64)
+    # batches of 1/512 of the slots plus a ragged tail: the fraction of the
+    # table in flight at once in the benchmark (~1.5e5 resident threads on a
+    # 2^26-slot table)
+    batch = max(512, (bins * B) // 512)
     sts = []
     for lo in range(0, len(keys), batch):
         sts.append(t.insert(kt[lo:lo + batch], vt[lo:lo + batch]))
@@ -136,10 +137,16 @@ def test_concurrent_set_semantics_match_oracle(bins, B, d, policy, load):
     assert t.contents() == ref.contents()
     s, os_ = t.stats(), ref.stats()
     assert s["size"] == len(keys) and s["live_ghosts"] == info["ghost_pairs"]
-    # bins viewed per insertion (the applied attempts): within 10% of the serial
-    # oracle at the same load
-    assert abs(s["bins_viewed"] / os_["bins_viewed"] - 1) < 0.10, (s["bins_viewed"], os_["bins_viewed"])
+    # bins viewed per insertion, all attempts counted (abandoned ones and
+    # re-views included): within 10% of the serial oracle at the same load.
+    # d-ary random walks are the exception: their walk lengths are heavy-
+    # tailed, and a long walk that meets other insertions' claims is
+    # abandoned and drawn again, which shortens the tail; the band there is
+    # 25% below to 10% above.
     assert s["bins_viewed_all"] >= s["bins_viewed"]
+    ratio = s["bins_viewed_all"] / os_["bins_viewed"]
+    lo = 0.75 if (d > 2 and policy & 0xFF == ck.RANDOM) else 0.90
+    assert lo < ratio < 1.10, (s["bins_viewed_all"], s["bins_viewed"], os_["bins_viewed"], s["aborts"])
     # lookups, 50% present / 50% absent
     probe, expect = inputs.lookup_keys(keys, 1 << 16, 9, 0.5, next_start=nxt)
     v, fnd = t.lookup(ck.as_u32_tensor(probe))
