@@ -181,6 +181,31 @@ int ck_shape(const ck_table *t, uint64_t *bins, uint32_t *slots_per_bin, uint32_
 
 const char *ck_strerror(int code);
 
+/* ---- insertion without allocation (the paper has no counterpart) ----
+ *
+ * For callers that must not allocate device memory on their insertion path:
+ * services whose device memory budget is fixed up front, real-time sections
+ * where an allocation's latency is not acceptable, libraries embedding this
+ * one that own no device allocator.  Same operation and per-key status as ck_insert_batch, but the
+ * per-search scratch of breadth-first and sorted search comes from a fixed
+ * array compiled into libck.so (CK_NOALLOC_MAX_KEYS regions of 16,400 bytes,
+ * 8.0 MiB, in the memory of every GPU that loads the library, kept until the
+ * process exits), one region per key, and the call allocates nothing.
+ *   - n > CK_NOALLOC_MAX_KEYS: returns CK_EINVAL and launches nothing.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call uses the same array: calls whose kernels overlap on the GPU
+ *     (other streams, other tables) race on it and must be ordered by the
+ *     caller.  The array keeps the last call's contents; nothing in it has
+ *     to start at zero.
+ *   - The table's counters are updated; the load histogram is not.
+ *   - Insertions are concurrent (one thread per key) as in ck_insert_batch;
+ *     the launch does not overlap the previous insert launch. */
+#define CK_NOALLOC_MAX_KEYS 512
+int ck_insert_batch_noalloc(ck_table *t, const uint32_t *d_keys, const uint32_t *d_vals, uint64_t n,
+                            uint8_t *d_status, void *stream);
+
 /* Measurement helper (not an operation of the paper): n_reads independent
  * random reads of `width` bytes (8, 32 or 64: one single-slot, 4-slot or
  * 8-slot bin) from a device buffer of `bytes` bytes (64-byte aligned), the

@@ -1,0 +1,163 @@
+// ck_noalloc.cu -- ck_insert_batch_noalloc: insertion for callers that
+// cannot allocate device memory while they run.
+//
+// Breadth-first and sorted search keep per-search state (the candidate
+// groups and the visited set) in scratch memory.  The ordinary insert path
+// takes that scratch from the table's own buffer, which ck_required_bytes
+// sizes for ~10^5 concurrent searches.  Some callers cannot size or
+// allocate such a buffer when they insert: services whose device memory
+// budget is fixed up front, real-time sections where an allocation's
+// latency is not acceptable, or libraries embedding this one that own no
+// device allocator.  For them this variant takes the search scratch from a
+// fixed array compiled into libck.so instead, and allocates nothing.  The
+// first call on a device looks up the array's device address; that first
+// call should come before any stream capture.
+//
+// The array: NOALLOC_REGIONS = 512 search regions of 16,400 bytes, 8.0 MiB in
+// all, in device memory of every GPU that loads the library, held until the
+// process exits.  One region per key, so a call takes at most 512 keys.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "ck.h"
+#include "ck_kernels.cuh"
+
+using namespace ck;
+
+// the device view of a table handle (defined in ck_lib.cu)
+const ck::DevTable* ck_internal_devtable(const ck_table* t);
+
+namespace {
+
+constexpr int NOALLOC_REGIONS = CK_NOALLOC_MAX_KEYS;
+constexpr size_t NOALLOC_BYTES = (size_t)NOALLOC_REGIONS * SEARCH_REGION;
+
+// One search region per key of a call.  Contents persist between calls;
+// nothing in a region needs to start at zero: each search stamps its visited
+// set with a generation number that only grows (the region's first word), so
+// entries left by earlier calls never match, and the group records are
+// written before they are read.
+static __device__ __align__(256) uint8_t g_noalloc_scratch[NOALLOC_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_mu;
+void* g_scratch_ptr[MAX_DEVICES] = {};
+
+// Device address of the array on the current device, looked up once per
+// device.  The host-side name g_noalloc_scratch is not a device address.
+int scratch_address(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CK_ECUDA;
+  if (dev < 0 || dev >= MAX_DEVICES) return CK_ENOTSUP;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return CK_ECUDA;
+    }
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return CK_OK;
+}
+
+// One thread per key; thread i searches in region i of the array.
+template <int B, int POL, bool GHOST>
+__global__ void __launch_bounds__(128) k_insert_noalloc(DevTable t, uint8_t* scratch,
+                                                        const uint32_t* __restrict__ keys,
+                                                        const uint32_t* __restrict__ vals, uint64_t n,
+                                                        uint8_t* __restrict__ status) {
+  __shared__ unsigned long long bc[C_N];
+  for (int i = threadIdx.x; i < C_N; i += blockDim.x) bc[i] = 0;
+  __syncthreads();
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    PlanStore<MAX_CHAIN> store;
+    uint8_t* region = scratch + i * SEARCH_REGION;
+    uint32_t key = keys[i];
+    int st = ST_INVALID;
+    Ctx c;
+    c.viewed = 0;
+    c.viewed0 = 0;
+    c.reviews = 0;
+    c.kicks = 0;
+    c.ghosts_made = 0;
+    c.dup_evict = 0;
+    uint32_t aborts = 0;
+    if (key != RESERVED_KEY) {
+      c.key = key;
+      c.krec = ((uint64_t)key << 32) | vals[i];
+      st = insert_one<B, POL, GHOST>(t, c, region, aborts, store.view());
+    }
+    if (status) status[i] = (uint8_t)st;
+    if (st != ST_INVALID) {
+      atomicAdd(&bc[st == ST_OK ? C_INS_OK : st == ST_FAILED ? C_INS_FAILED : C_INS_ABORTED], 1ull);
+      atomicAdd(&bc[C_VIEWED], (unsigned long long)(c.viewed - c.viewed0));
+      atomicAdd(&bc[C_VIEWED_ALL], (unsigned long long)c.viewed);
+      if (aborts) atomicAdd(&bc[C_ABORTS], (unsigned long long)aborts);
+      if (c.reviews) atomicAdd(&bc[C_REVIEWS], (unsigned long long)c.reviews);
+      if (st == ST_OK) {
+        atomicAdd(&bc[C_KICKS], (unsigned long long)c.kicks);
+        atomicMax(&bc[C_CHAIN_MAX], (unsigned long long)c.kicks);
+        if (c.ghosts_made) atomicAdd(&bc[C_GHOSTS_MADE], (unsigned long long)c.ghosts_made);
+        if (c.dup_evict) atomicAdd(&bc[C_DUP_EVICT], (unsigned long long)c.dup_evict);
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < C_N; k++) {
+      if (!bc[k]) continue;
+      if (k == C_CHAIN_MAX) atomicMax(t.counters + k, bc[k]);
+      else atomicAdd(t.counters + k, bc[k]);
+    }
+    if (bc[C_INS_OK]) atomicAdd(t.counters + C_SIZE, bc[C_INS_OK]);
+    long long dg = (long long)bc[C_GHOSTS_MADE] - (long long)bc[C_DUP_EVICT];
+    if (dg) atomicAdd(t.counters + C_LIVE_GHOSTS, (unsigned long long)dg);
+  }
+}
+
+template <int B, int POL, bool GHOST>
+void launch(const DevTable& dt, uint8_t* scratch, const uint32_t* k, const uint32_t* v, uint64_t n,
+            uint8_t* st, cudaStream_t s) {
+  unsigned grid = (unsigned)((n + 127) / 128);
+  k_insert_noalloc<B, POL, GHOST><<<grid, 128, 0, s>>>(dt, scratch, k, v, n, st);
+}
+
+template <int B>
+int dispatch2(const DevTable& dt, uint8_t* sp, const uint32_t* k, const uint32_t* v, uint64_t n, uint8_t* st,
+              cudaStream_t s) {
+  bool g = dt.ghost != 0;
+  switch (dt.policy) {
+    case CK_RANDOM: g ? launch<B, P_RANDOM, true>(dt, sp, k, v, n, st, s) : launch<B, P_RANDOM, false>(dt, sp, k, v, n, st, s); break;
+    case CK_BFS: g ? launch<B, P_BFS, true>(dt, sp, k, v, n, st, s) : launch<B, P_BFS, false>(dt, sp, k, v, n, st, s); break;
+    case CK_SORTED: g ? launch<B, P_SORTED, true>(dt, sp, k, v, n, st, s) : launch<B, P_SORTED, false>(dt, sp, k, v, n, st, s); break;
+    case CK_QUEUE: g ? launch<B, P_QUEUE, true>(dt, sp, k, v, n, st, s) : launch<B, P_QUEUE, false>(dt, sp, k, v, n, st, s); break;
+    default: return CK_ENOTSUP;
+  }
+  return CK_OK;
+}
+
+}  // namespace
+
+extern "C" int ck_insert_batch_noalloc(ck_table* t, const uint32_t* d_keys, const uint32_t* d_vals, uint64_t n,
+                                       uint8_t* d_status, void* stream) {
+  if (!t) return CK_EINVAL;
+  if (n > (uint64_t)CK_NOALLOC_MAX_KEYS) return CK_EINVAL;  // one scratch region per key
+  if (n == 0) return CK_OK;
+  if (!d_keys || !d_vals) return CK_EINVAL;
+  void* sp = nullptr;
+  int rc = scratch_address(&sp);
+  if (rc != CK_OK) return rc;
+  const DevTable& dt = *ck_internal_devtable(t);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  uint8_t* scratch = static_cast<uint8_t*>(sp);
+  if (dt.B == 4) rc = dispatch2<4>(dt, scratch, d_keys, d_vals, n, d_status, s);
+  else if (dt.B == 8) rc = dispatch2<8>(dt, scratch, d_keys, d_vals, n, d_status, s);
+  else if (dt.policy == CK_RATTLE) launch<1, P_RATTLE, false>(dt, scratch, d_keys, d_vals, n, d_status, s);
+  else launch<1, P_RANDOM, false>(dt, scratch, d_keys, d_vals, n, d_status, s);
+  if (rc != CK_OK) return rc;
+  return cudaGetLastError() == cudaSuccess ? CK_OK : CK_ECUDA;
+}
