@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -49,6 +50,10 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-policies", action="store_true", help="skip the per-policy fills")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-multi", action="store_true", help="skip the batched form (4096 tables)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving form")
+    ap.add_argument("--only", choices=["serve", "multi", "policies"],
+                    help="run one side section alone and print its JSON (diagnostics; no bench line)")
     return ap.parse_args()
 
 
@@ -86,14 +91,15 @@ class Clocks:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % gpu_index)
+        self.path = os.environ.get("CK_CLOCKS_CSV") or os.path.join(
+            tempfile.gettempdir(), "ck_clocks_gpu%d_%d.csv" % (gpu_index, os.getpid()))
 
     def start(self):
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -223,15 +229,16 @@ def policy_fills(torch, ck, stream, base_keys):
         torch.cuda.empty_cache()
     del kt, vt, st
     # 8-slot bins at 0.99 and the d-ary tables of the same slot count
+    lookup_cache = {}
     for name, bins, b, d, pol, load, cap in (
             ("queue_b8_0.99", 1 << 23, 8, 2, ck.QUEUE, 0.99, 500),
             ("random_b8_0.99", 1 << 23, 8, 2, ck.RANDOM, 0.99, 500),
             ("random_d3_0.90", 1 << 26, 1, 3, ck.RANDOM, 0.90, 4096),
             ("rattle_d3_0.90", 1 << 26, 1, 3, ck.RATTLE, 0.90, 500),
-            ("random_d4_0.96", 1 << 26, 1, 4, ck.RANDOM, 0.96, 4096),
-            ("rattle_d4_0.96", 1 << 26, 1, 4, ck.RATTLE, 0.96, 500),
             ("random_d3_0.90_hash1", 1 << 26, 1, 3, ck.RANDOM | 0x10000, 0.90, 4096),
             ("rattle_d3_0.90_hash1", 1 << 26, 1, 3, ck.RATTLE | 0x10000, 0.90, 500),
+            ("random_d4_0.96", 1 << 26, 1, 4, ck.RANDOM, 0.96, 4096),
+            ("rattle_d4_0.96", 1 << 26, 1, 4, ck.RATTLE, 0.96, 500),
             ("random_d4_0.96_hash1", 1 << 26, 1, 4, ck.RANDOM | 0x10000, 0.96, 4096),
             ("rattle_d4_0.96_hash1", 1 << 26, 1, 4, ck.RATTLE | 0x10000, 0.96, 500)):
         n = inputs.load_target(bins * b, load)
@@ -250,7 +257,11 @@ def policy_fills(torch, ck, stream, base_keys):
                "bins_viewed_per_insert": round(s["bins_viewed_per_insert"], 4),
                "chain_max": s["chain_max"], "failed": s["inserts_failed"], "aborted": s["inserts_aborted"]}
         if d > 2:
-            lk, expect = inputs.lookup_keys(keys, N_LOOKUP, 2, 0.5, next_start=nxt)
+            ck_key = (bins, d, load)
+            if ck_key not in lookup_cache:
+                lookup_cache.clear()
+                lookup_cache[ck_key] = inputs.lookup_keys(keys, N_LOOKUP, 2, 0.5, next_start=nxt)
+            lk, expect = lookup_cache[ck_key]
             lkt = ck.as_u32_tensor(lk)
             v = torch.empty(N_LOOKUP, dtype=torch.int32, device="cuda")
             f = torch.empty(N_LOOKUP, dtype=torch.uint8, device="cuda")
@@ -267,6 +278,173 @@ def policy_fills(torch, ck, stream, base_keys):
         t.close()
         del t, kt, vt, st
         torch.cuda.empty_cache()
+    return out
+
+
+def multi_form(torch, ck, stream):
+    """Batched form: 4096 independent tables (bins log-uniform in [2^10, 2^18],
+    4 or 8 slots, keys from seed 8 + table id) filled to 0.95 with
+    queue-kicking, as one autotuned persistent launch versus one launch per
+    table, each replayed from a CUDA graph."""
+    from paper_1605_05236_gb300 import autotune, inputs
+    from paper_1605_05236_gb300 import multi as M
+    t0 = time.perf_counter()
+    bins, slots = inputs.multi_shapes(4096, seed=7)
+    keys, vals, n_keys = inputs.multi_keys(bins, slots, 0.95, seed0=8)
+    gen_s = time.perf_counter() - t0
+    kt, vt = ck.as_u32_tensor(keys), ck.as_u32_tensor(vals)
+    st = torch.empty(len(keys), dtype=torch.uint8, device="cuda")
+    mt = M.MultiTable(bins, slots, n_keys, ck.QUEUE, seed=1)
+    best, trials = autotune.tune(mt, kt, vt, st, stream)
+
+    def graph_ms(per_table):
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            mt.clear(side)
+            mt.insert(kt, vt, st, per_table=per_table, stream=side)  # warm
+        side.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            mt.clear(side)
+            mt.insert(kt, vt, st, per_table=per_table, stream=side)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g.replay()
+        torch.cuda.synchronize()
+        best_ms = None
+        for _ in range(3):
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best_ms = ms if best_ms is None else min(best_ms, ms)
+        ok = bool((st == 0).all().item())
+        s = mt.stats()
+        del g
+        return best_ms, ok, s
+
+    ms_b, ok_b, s_b = graph_ms(False)
+    ms_p, ok_p, s_p = graph_ms(True)
+    n = len(keys)
+    out = {"tables": 4096, "keys": n, "slots": int((bins * slots).sum()), "gen_s": round(gen_s, 1),
+           "autotuned": best, "tuning": [{"cfg": c, "ms": round(m, 3)} for c, m in trials],
+           "batched": {"ms": round(ms_b, 3), "m_inserts_per_s": round(n / ms_b / 1e3, 1), "all_inserted": ok_b,
+                       "bins_viewed_per_insert": round(s_b["bins_viewed_per_insert"], 4), "size": s_b["size"]},
+           "per_table": {"ms": round(ms_p, 3), "m_inserts_per_s": round(n / ms_p / 1e3, 1), "all_inserted": ok_p,
+                         "bins_viewed_per_insert": round(s_p["bins_viewed_per_insert"], 4), "size": s_p["size"],
+                         "launches": 4096},
+           "speedup": round(ms_p / ms_b, 3)}
+    mt.close()
+    del kt, vt, st, mt
+    torch.cuda.empty_cache()
+    return out
+
+
+SERVE_BINS = 1 << 26
+SERVE_PREFILL = 255013683  # floor(0.95 * 2^28)
+
+
+def serve_form(torch, ck, stream):
+    """Serving form: a 2^26 x 4 table (2 GiB of slots) prefilled to 0.95
+    (255,013,683 keys of seed 5) takes a trace of 4096 requests (Poisson
+    arrivals at 20k requests/ms, sizes log-uniform 1..2^16 keys, mixes
+    lookup/insert/delete 75/20/5 and 50/25/25, seed 11), run (a) as plain
+    sequential bulk calls and (b) through the continuous-batching server,
+    each at the trace's own rate (a burst far above either's capacity) and
+    open-loop at 0.8x the capacity the sequential run showed; the server
+    also at 0.8x its own capacity.  The table is refilled before every run, so every
+    run starts from the same state, and its results must equal the trace's."""
+    from paper_1605_05236_gb300 import inputs, serve
+    t0 = time.perf_counter()
+    keys, _ = inputs.distinct_keys(SERVE_PREFILL, 5)
+    vals = inputs.values_for(keys)
+    gen_s = time.perf_counter() - t0
+    table = ck.CuckooTable(SERVE_BINS, B, 2, ck.QUEUE, seed=1)
+    kt, vt = ck.as_u32_tensor(keys), ck.as_u32_tensor(vals)
+    st = torch.empty(len(keys), dtype=torch.uint8, device="cuda")
+
+    def prefill():
+        fill_once(torch, ck, table, kt, vt, st, stream)
+        torch.cuda.synchronize()
+
+    def summary(tr, res, scale):
+        v, s, lat = res
+        arrive = tr["arrive_ns"].astype(np.float64) * scale
+        span_s = float(np.max(arrive + lat)) * 1e-9
+        n_keys = len(tr["keys"])
+        return {"m_keys_per_s": round(n_keys / span_s / 1e6, 1), "k_req_per_s": round(len(lat) / span_s / 1e3, 1),
+                "span_ms": round(span_s * 1e3, 3), "p50_us": round(float(np.percentile(lat, 50)) / 1e3, 1),
+                "p99_us": round(float(np.percentile(lat, 99)) / 1e3, 1)}
+
+    def check(tr, res):
+        """None when every result equals the trace's, else mismatch counts."""
+        v, s, _ = res
+        op = np.repeat(tr["op"], tr["n_keys"].astype(np.int64))
+        look = op == 0
+        hit = look & (tr["expect"] == 1)
+        want = np.where(look, tr["expect"], np.where(op == 1, 0, 1)).astype(np.uint8)
+        bad = s != want
+        bad_val = int((v[hit] != tr["vals"][hit]).sum())
+        if not bad.any() and not bad_val:
+            return None
+        out = {"value_mismatch": bad_val}
+        for name, k in (("lookup", 0), ("insert", 1), ("delete", 2)):
+            sel = bad & (op == k)
+            if sel.any():
+                st_vals, cnt = np.unique(s[sel], return_counts=True)
+                out[name] = {"wrong": int(sel.sum()), "statuses": {int(a): int(b) for a, b in zip(st_vals, cnt)}}
+        return out
+
+    cfg = {"wave_keys": 1 << 20, "wave_slots": 4, "load_hi": 0.97}
+    out = {"table": "2^26 x 4 (2 GiB) prefilled to 0.95 (255,013,683 keys)", "requests": 4096,
+           "sizes": "log-uniform 1..2^16 keys", "arrivals": "Poisson, 20k requests/ms", "server": cfg,
+           "gen_s": round(gen_s, 1)}
+    for mix in [(75, 20, 5), (50, 25, 25)]:
+        tr = inputs.serving_trace(keys, 4096, mix, seed=11, max_log2=16)
+        rec = {"keys": int(len(tr["keys"])), "mix": "%d/%d/%d" % mix}
+        runs, run_names = [], ["sequential_trace_rate"]
+        prefill()
+        seq = serve.replay_sequential(table, tr, time_scale=1.0)
+        runs.append(seq)
+        rec["sequential_trace_rate"] = summary(tr, seq, 1.0)
+
+        def run(name, sc, server):
+            prefill()
+            if server:
+                srv = serve.Server(table, **cfg)
+                res = srv.replay(tr, time_scale=sc)
+                info = srv.info()
+                srv.close()
+            else:
+                res, info = serve.replay_sequential(table, tr, time_scale=sc), None
+            runs.append(res)
+            run_names.append(name)
+            rec[name] = summary(tr, res, sc)
+            if info:
+                rec[name]["waves"] = info["waves"]
+                rec[name]["busy_rejects"] = info["busy_rejects"]
+
+        def scale_for(rate):  # time scale that makes the trace arrive at `rate` requests/s
+            return (len(tr["op"]) / rate * 1e9) / max(1.0, float(tr["arrive_ns"][-1]))
+
+        run("server_trace_rate", 1.0, True)
+        cap_seq = len(tr["op"]) / (rec["sequential_trace_rate"]["span_ms"] * 1e-3)  # requests/s
+        cap_srv = len(tr["op"]) / (rec["server_trace_rate"]["span_ms"] * 1e-3)
+        run("sequential_0.8x_seq_capacity", scale_for(0.8 * cap_seq), False)
+        run("server_0.8x_seq_capacity", scale_for(0.8 * cap_seq), True)
+        run("server_0.8x_server_capacity", scale_for(0.8 * cap_srv), True)
+        rec["capacity_k_req_per_s"] = {"sequential": round(cap_seq / 1e3, 1), "server": round(cap_srv / 1e3, 1)}
+        bad = {name: check(tr, r) for name, r in zip(run_names, runs)}
+        rec["results_exact"] = all(b is None for b in bad.values())
+        if not rec["results_exact"]:
+            rec["mismatches"] = {k: b for k, b in bad.items() if b is not None}
+        rec["throughput_speedup"] = round(rec["sequential_trace_rate"]["span_ms"] /
+                                          rec["server_trace_rate"]["span_ms"], 3)
+        out["mix_%d_%d_%d" % mix] = rec
+    table.close()
+    del kt, vt, st
+    torch.cuda.empty_cache()
     return out
 
 
@@ -289,6 +467,27 @@ def cpu_baseline():
                       "(%d keys, %.1f s); bins viewed/insert %.4f" % (n, dt, s["bins_viewed"] / n)}
 
 
+def rank_seed(rank: int) -> int:
+    """Key seed of a rank: each rank fills its own table with its own keys
+    (independent shards, weak scaling)."""
+    return 1 + 1000 * rank
+
+
+def max_over_ranks(torch, values, world, device):
+    """Element-wise maximum of per-rank timings (the slowest rank sets the
+    job's time); no-op on one rank."""
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def job_rate(units_per_rank, steps, ms, world):
+    """Whole-job throughput in M units/s: every rank processed
+    units_per_rank per step, and the job took `ms` (max over ranks)."""
+    return world * units_per_rank * steps / (ms * 1e-3) / 1e6
+
+
 def run_gpu(args, rank, world, local):
     import torch
     from paper_1605_05236_gb300 import ck
@@ -299,7 +498,7 @@ def run_gpu(args, rank, world, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     ck.load()
     stream = torch.cuda.current_stream()
-    seed = 1 + 1000 * rank  # each rank fills its own table: independent shards (weak scaling)
+    seed = rank_seed(rank)
     keys, vals, lk, expect, dk = workload(seed)
     n = len(keys)
     kt, vt = ck.as_u32_tensor(keys), ck.as_u32_tensor(vals)
@@ -360,14 +559,11 @@ def run_gpu(args, rank, world, local):
     vals_exact = bool(torch.equal(lv.cpu()[present], want[present]))
     deletes_exact = bool((df == 1).all().item())
 
-    times = torch.tensor([total_ms, fill_ms, look_ms, del_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(times, op=torch.distributed.ReduceOp.MAX)
-    total_ms, fill_ms, look_ms, del_ms = [float(x) for x in times.cpu()]
+    total_ms, fill_ms, look_ms, del_ms = max_over_ranks(torch, [total_ms, fill_ms, look_ms, del_ms], world, "cuda")
     K = args.steps
-    value = world * n * K / (fill_ms * 1e-3) / 1e6
-    lookups_mops = world * N_LOOKUP * K / (look_ms * 1e-3) / 1e6
-    deletes_mops = world * N_DELETE * K / (del_ms * 1e-3) / 1e6
+    value = job_rate(n, K, fill_ms, world)
+    lookups_mops = job_rate(N_LOOKUP, K, look_ms, world)
+    deletes_mops = job_rate(N_DELETE, K, del_ms, world)
 
     # roofline of the dominant kernel (the insert kernel: it takes most of the step)
     hbm, peak_kind = measured_peaks()
@@ -417,6 +613,10 @@ def run_gpu(args, rank, world, local):
     torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_policies:
         out["policies"] = policy_fills(torch, ck, stream, (keys, vals))
+    if rank == 0 and world == 1 and not args.no_multi:
+        out["batched_form"] = multi_form(torch, ck, stream)
+    if rank == 0 and world == 1 and not args.no_serve:
+        out["serving_form"] = serve_form(torch, ck, stream)
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline()
     if world > 1:
@@ -527,11 +727,26 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+def run_section(name):
+    import torch
+    from paper_1605_05236_gb300 import ck
+    ck.load()
+    stream = torch.cuda.current_stream()
+    if name == "serve":
+        return {"serving_form": serve_form(torch, ck, stream)}
+    if name == "multi":
+        return {"batched_form": multi_form(torch, ck, stream)}
+    keys, vals, _, _, _ = workload(rank_seed(0))
+    return {"policies": policy_fills(torch, ck, stream, (keys, vals))}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif args.only:
+        out = run_section(args.only)
     else:
         out = run_gpu(args, rank, world, local)
     if rank == 0 and out is not None:

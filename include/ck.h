@@ -141,14 +141,19 @@ int ck_insert_batch_ex(ck_table *t, const uint32_t *d_keys, const uint32_t *d_va
                        uint8_t *d_status, uint32_t *d_viewed, uint32_t flags, void *stream);
 
 /* Look up n keys (Sec. 1: a present key is in one of its bins).  Writes
- * d_vals_out[i] (0 when absent) and d_found[i] in {0,1}; either nullable. */
+ * d_vals_out[i] (0 when absent) and d_found[i] in {0,1}; either nullable.
+ * The reads are not validated against writers: call it while no insertion
+ * or delete on this table is in flight on another stream (the serving
+ * form's lookups are validated and may overlap writers). */
 int ck_lookup_batch(ck_table *t, const uint32_t *d_keys, uint64_t n, uint32_t *d_vals_out,
                     uint8_t *d_found, void *stream);
 
 /* Delete n keys (Sec. 1), every copy of a ghost pair included.  d_found[i]
- * (nullable) = 1 if this call removed the key.  A slot claimed by an
- * in-flight insertion is not waited on (Sec. 8): the delete retries a
- * bounded number of times, then reports 2 in d_found. */
+ * (nullable) = 1 if this call removed the key, 0 if it was absent.  Safe
+ * beside insertions running on other streams: a slot claimed by an
+ * in-flight insertion (Sec. 8) is waited out with backoff, and a miss is
+ * reported only after the key's bins were read unclaimed and unchanged;
+ * after 1024 such retries the key gets 2 (not resolved). */
 int ck_delete_batch(ck_table *t, const uint32_t *d_keys, uint64_t n, uint8_t *d_found,
                     void *stream);
 
@@ -205,6 +210,139 @@ const char *ck_strerror(int code);
 #define CK_NOALLOC_MAX_KEYS 512
 int ck_insert_batch_noalloc(ck_table *t, const uint32_t *d_keys, const uint32_t *d_vals, uint64_t n,
                             uint8_t *d_status, void *stream);
+
+/* ---- batched form: many independent two-choice tables, one launch ----
+ *
+ * Thousands of independent tables of uneven sizes in one device buffer,
+ * filled by one persistent launch (a queue of key tiles over all tables)
+ * instead of one launch per table.  Each table behaves exactly like a
+ * ck_table with the same shape and policy: the same kick-out policies
+ * (RANDOM or QUEUE, optionally | GHOST), claim flags and back-to-front
+ * chains (Sec. 3-8), the default hash seeds, and the draw seed seed + i for
+ * table i.  Keys of table i are key_offset .. key_offset + n_keys - 1 of the
+ * shared key/value/status arrays (device pointers). */
+typedef struct ck_multi_desc {
+  uint64_t bins;          /* n_bins of this table (>= 2, < 2^32; need not be a power of two) */
+  uint32_t slots_per_bin; /* 4 or 8 */
+  uint32_t pad;
+  uint64_t key_offset;
+  uint64_t n_keys;
+} ck_multi_desc;
+
+typedef struct ck_multi ck_multi;
+
+/* Device bytes for n tables with these descriptors (0 when invalid). */
+size_t ck_multi_required_bytes(const ck_multi_desc *h_desc, uint32_t n_tables);
+
+/* Create the tables in one caller-owned device buffer (256-byte aligned,
+ * >= ck_multi_required_bytes); clears them on `stream`. */
+int ck_multi_create_on(ck_multi **out, void *dev_buf, size_t bytes, const ck_multi_desc *h_desc,
+                       uint32_t n_tables, uint32_t policy, uint64_t seed, void *stream);
+
+/* Launch-shape knobs (chosen by the autotuner): keys per tile (>= 256),
+ * threads per block (64/128/256), resident blocks per SM (0 = as many as
+ * fit), chain cap of every table. */
+#define CK_MULTI_TILE 1
+#define CK_MULTI_BLOCK 2
+#define CK_MULTI_BLOCKS_PER_SM 3
+#define CK_MULTI_CHAIN_CAP 4
+int ck_multi_set_param(ck_multi *m, int key, int64_t value);
+
+/* Insert every table's keys: one persistent launch; blocks take tiles in
+ * the order of a list interleaved over the tables.  Asynchronous. */
+int ck_multi_insert(ck_multi *m, const uint32_t *d_keys, const uint32_t *d_vals, uint8_t *d_status,
+                    void *stream);
+
+/* The reference path: one single-table insert launch per table (the same
+ * per-insertion code), for comparison. */
+int ck_multi_insert_per_table(ck_multi *m, const uint32_t *d_keys, const uint32_t *d_vals,
+                              uint8_t *d_status, void *stream);
+
+/* Look up n keys, key i in table d_table[i] (outputs as ck_lookup_batch). */
+int ck_multi_lookup(ck_multi *m, const uint32_t *d_table, const uint32_t *d_keys, uint64_t n,
+                    uint32_t *d_vals_out, uint8_t *d_found, void *stream);
+
+/* Counters of one table / summed over all tables (synchronise). */
+int ck_multi_table_stats(ck_multi *m, uint32_t table, ck_stats_t *out);
+int ck_multi_stats(ck_multi *m, ck_stats_t *out);
+
+/* Copy one table out (as ck_export; synchronous). */
+int ck_multi_export(ck_multi *m, uint32_t table, uint64_t *h_slots, uint32_t *h_meta);
+
+/* Empty every table (asynchronous) / free the handle (not the buffer). */
+int ck_multi_clear(ck_multi *m, void *stream);
+void ck_multi_destroy(ck_multi *m);
+
+/* ---- serving form: a continuous-batching request loop ----
+ *
+ * A server owns a resident table (created with ck_create/ck_create_on)
+ * and two host threads.  Requests (lookup, insert or delete of n keys in
+ * host memory) are submitted as they arrive; the scheduler merges every
+ * pending request that fits into the next free wave slot (keys copied into
+ * pinned staging, one device batch per kind), launches the three kinds on
+ * three streams, and goes on forming the next wave while earlier ones run
+ * (continuous batching).  A completion thread copies results out and
+ * timestamps each request.  Inserts are admitted only while the table's
+ * load (live keys + admitted inserts) stays at or below load_hi; an insert
+ * that waits longer than max_defer_us completes with CK_ST_BUSY.  Wave
+ * staging is sized to fit in hbm_fraction of the device memory free at
+ * creation (fewer slots if needed).  Lookups in the server validate their
+ * reads against concurrent writers: a miss counts only when the key's bins
+ * were unclaimed and unchanged across the read (status 2 after 1024
+ * retries: not resolved).  The table must not be used by other calls while
+ * a server owns it.  The paper has no serving loop; it is the continuous
+ * form of its bulk operations (Sec. 8 concurrency). */
+#define CK_OP_LOOKUP 0
+#define CK_OP_INSERT 1
+#define CK_OP_DELETE 2
+#define CK_ST_BUSY 4     /* insert not admitted: the table stayed above load_hi */
+
+typedef struct ck_server_config {
+  uint64_t wave_keys;    /* keys per kind per wave (default 2^20; a request may not exceed it) */
+  uint32_t wave_slots;   /* waves in flight (default 4) */
+  uint32_t pad;
+  double load_hi;        /* admission bound for inserts (default 0.97) */
+  uint64_t max_defer_us; /* longest wait of a deferred insert (default 20000) */
+  double hbm_fraction;   /* share of free device memory the staging may take (default 0.25) */
+} ck_server_config;
+
+typedef struct ck_server ck_server;
+
+/* cfg may be NULL for the defaults.  Synchronises the table's stream. */
+int ck_server_create(ck_server **out, ck_table *t, const ck_server_config *cfg);
+
+/* Queue a request; h_* are host buffers that must stay valid until the
+ * request completes.  t_arrive_ns (0 = now, ck_now_ns clock) is the arrival
+ * time latency is measured from.  *ticket is waited on with ck_server_wait. */
+int ck_server_submit(ck_server *s, uint32_t op, const uint32_t *h_keys, const uint32_t *h_vals, uint64_t n,
+                     uint32_t *h_vals_out, uint8_t *h_status_out, int64_t t_arrive_ns, void **ticket);
+
+/* Block until the request is done (frees the ticket); *latency_ns =
+ * completion - arrival. */
+int ck_server_wait(ck_server *s, void *ticket, int64_t *latency_ns);
+
+/* Monotonic clock of the server, nanoseconds. */
+int64_t ck_now_ns(void);
+
+/* Open-loop replay of a trace: request i (op[i]; keys key_off[i] ..
+ * key_off[i] + n_keys[i] - 1 of the host arrays) is submitted at
+ * arrive_ns[i] after the call starts; waits for all; per-request latency. */
+int ck_server_replay(ck_server *s, uint64_t n_req, const uint32_t *op, const uint64_t *key_off,
+                     const uint64_t *n_keys, const int64_t *arrive_ns, const uint32_t *keys,
+                     const uint32_t *vals, uint32_t *vals_out, uint8_t *status_out, int64_t *latency_ns);
+
+/* The same trace as plain sequential bulk calls on one stream (request i
+ * starts once it has arrived and request i-1 is done): the reference. */
+int ck_replay_sequential(ck_table *t, uint64_t n_req, const uint32_t *op, const uint64_t *key_off,
+                         const uint64_t *n_keys, const int64_t *arrive_ns, const uint32_t *keys,
+                         const uint32_t *vals, uint32_t *vals_out, uint8_t *status_out,
+                         int64_t *latency_ns, void *stream);
+
+/* Waves launched, inserts refused, current load, wave slots. */
+int ck_server_info(ck_server *s, uint64_t *waves, uint64_t *busy_rejects, double *load, uint32_t *wave_slots);
+
+/* Stop the threads (after draining) and free the server (not the table). */
+void ck_server_destroy(ck_server *s);
 
 /* Measurement helper (not an operation of the paper): n_reads independent
  * random reads of `width` bytes (8, 32 or 64: one single-slot, 4-slot or

@@ -186,6 +186,34 @@ __device__ __forceinline__ void fence_release() {
   cuda::atomic_thread_fence(cuda::memory_order_release, cuda::thread_scope_device);
 }
 
+__device__ __forceinline__ void fence_acquire() {
+  cuda::atomic_thread_fence(cuda::memory_order_acquire, cuda::thread_scope_device);
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// A read of a bin's slots that saw no claim bit in the bin's metadata word,
+// and finds the word unchanged when it is read again after the slots, saw
+// no writer: every slot write happens under a claim, and every release
+// advances the bin's version.  This is how a miss is proven while
+// insertions run (a key moving between its own bins is written to the new
+// bin before it leaves the old one, but two separate reads can still fall
+// on either side of the move).
+__device__ __forceinline__ bool unchanged_since(const uint32_t* meta, const uint32_t* bins, const uint32_t* seen,
+                                                uint32_t nb, uint32_t claim_bits) {
+  fence_acquire();
+  bool ok = true;
+  for (uint32_t j = 0; j < nb; j++) {
+    uint32_t now = ld_relaxed(meta + bins[j]);
+    ok &= now == seen[j] && (seen[j] & claim_bits) == 0;
+  }
+  return ok;
+}
+
 __device__ __forceinline__ bool cas_acquire(uint32_t* p, uint32_t expected, uint32_t desired) {
   uint32_t old;
   asm volatile("atom.acquire.gpu.global.cas.b32 %0, [%1], %2, %3;"

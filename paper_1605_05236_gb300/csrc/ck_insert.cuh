@@ -28,39 +28,13 @@ enum Kind : uint8_t { K_MOVE = 0, K_DUPTERM = 1, K_TWIN = 2, K_GHOST = 3 };
 // a packed descriptor -- bits 0-31 bin, 32-34 slot, 35-36 kind, 37
 // hit-counter increment, 40-47 rattle counter of the displaced key, 48-55
 // rattle counter of the incoming key -- and the record the slot held when it
-// was claimed.  Entries live in local memory (MAX_CHAIN of them, the
-// concurrent kernel) or in table scratch (LONG_CHAIN: the serial replay and
-// chains longer than MAX_CHAIN).
-struct Plan {
-  uint64_t* e;  // 2 * cap words
-  int n;
-  int cap;
-};
-
+// was claimed.  Beyond the first REG_ENTRIES (registers), entries live in
+// local memory (MAX_CHAIN of them, the concurrent kernel) or in table
+// scratch (LONG_CHAIN: the serial replay and chains longer than MAX_CHAIN).
 template <int N>
 struct PlanStore {
   alignas(16) uint64_t e[2 * N];  // entries are stored as 16-byte vectors
-  __device__ __forceinline__ Plan view() {
-    Plan p{e, 0, N};
-    return p;
-  }
 };
-
-__device__ __forceinline__ Plan plan_in(uint8_t* r) {
-  Plan p{reinterpret_cast<uint64_t*>(r), 0, LONG_CHAIN};
-  return p;
-}
-
-// p.e is 16-byte aligned: a PlanStore array or a 256-byte aligned scratch region.
-__device__ __forceinline__ void put_entry(Plan& p, uint64_t desc, uint64_t content) {
-  ulonglong2 v;
-  v.x = desc;
-  v.y = content;
-  *reinterpret_cast<ulonglong2*>(p.e + 2 * p.n) = v;
-  p.n++;
-}
-__device__ __forceinline__ uint64_t desc_at(const Plan& p, int i) { return p.e[2 * i]; }
-__device__ __forceinline__ uint64_t content_at(const Plan& p, int i) { return p.e[2 * i + 1]; }
 
 __device__ __forceinline__ uint64_t pack_entry(uint32_t bin, int slot, int kind, bool hit, uint32_t old_r,
                                                uint32_t new_r) {
@@ -74,6 +48,15 @@ __device__ __forceinline__ bool e_hit(uint64_t e) { return (e >> 37) & 1u; }
 __device__ __forceinline__ uint32_t e_old_r(uint64_t e) { return (uint32_t)(e >> 40) & 255u; }
 __device__ __forceinline__ uint32_t e_new_r(uint64_t e) { return (uint32_t)(e >> 48) & 255u; }
 
+// The first REG_ENTRIES entries of a plan stay in registers (most chains
+// are one or two slots long); the rest go to memory at pe, indexed by entry
+// number (the first REG_ENTRIES places there stay unused).
+#ifndef CK_REG_ENTRIES
+#define CK_REG_ENTRIES 2
+#endif
+constexpr int REG_ENTRIES = CK_REG_ENTRIES;
+static_assert(REG_ENTRIES >= 0 && REG_ENTRIES <= 2, "at most two plan entries in registers");
+
 struct Ctx {
   uint32_t key;
   uint64_t krec;
@@ -86,11 +69,49 @@ struct Ctx {
   uint32_t draws;    // random draws of the current attempt
   uint32_t ghosts_made;
   uint32_t dup_evict;
-  Plan* plan;
-  Plan lp;      // scratch plan, once the local one is outgrown
-  int long_id;  // its index in the table's pool, or -1
+  // the plan, by value so the context can live in registers: entries
+  // 0 .. REG_ENTRIES-1 in r*, the others at pe (16-byte aligned); pn of pcap used
+  uint64_t r0d, r0c, r1d, r1c;
+  uint64_t* pe;
+  int pn;
+  int pcap;
+  int long_id;    // scratch plan in use (index in the table's pool), or -1
   uint64_t held;  // d-ary walks: the record in hand
 };
+
+__device__ __forceinline__ void set_entry(Ctx& c, int i, uint64_t desc, uint64_t content) {
+  if (REG_ENTRIES > 0 && i == 0) {
+    c.r0d = desc;
+    c.r0c = content;
+  } else if (REG_ENTRIES > 1 && i == 1) {
+    c.r1d = desc;
+    c.r1c = content;
+  } else {
+    ulonglong2 v;
+    v.x = desc;
+    v.y = content;
+    *reinterpret_cast<ulonglong2*>(c.pe + 2 * i) = v;
+  }
+}
+__device__ __forceinline__ void set_content(Ctx& c, int i, uint64_t content) {
+  if (REG_ENTRIES > 0 && i == 0) c.r0c = content;
+  else if (REG_ENTRIES > 1 && i == 1) c.r1c = content;
+  else c.pe[2 * i + 1] = content;
+}
+__device__ __forceinline__ void put_entry(Ctx& c, uint64_t desc, uint64_t content) {
+  set_entry(c, c.pn, desc, content);
+  c.pn++;
+}
+__device__ __forceinline__ uint64_t desc_at(const Ctx& c, int i) {
+  if (REG_ENTRIES > 0 && i == 0) return c.r0d;
+  if (REG_ENTRIES > 1 && i == 1) return c.r1d;
+  return c.pe[2 * i];
+}
+__device__ __forceinline__ uint64_t content_at(const Ctx& c, int i) {
+  if (REG_ENTRIES > 0 && i == 0) return c.r0c;
+  if (REG_ENTRIES > 1 && i == 1) return c.r1c;
+  return c.pe[2 * i + 1];
+}
 
 // Scratch plans for chains longer than a thread's local plan: a pool with a
 // busy flag per plan.  Taking one never waits unboundedly: after a bounded
@@ -118,11 +139,10 @@ __device__ __forceinline__ bool grow_plan(const DevTable& t, Ctx& c) {
   if (c.long_id >= 0) return false;
   int id = acquire_long(t, c.key);
   if (id < 0) return false;
-  Plan lp = plan_in(t.long_scratch + (uint64_t)id * LONG_REGION);
-  for (int i = 0; i < 2 * c.plan->n; i++) lp.e[i] = c.plan->e[i];
-  lp.n = c.plan->n;
-  c.lp = lp;
-  c.plan = &c.lp;
+  uint64_t* le = reinterpret_cast<uint64_t*>(t.long_scratch + (uint64_t)id * LONG_REGION);
+  for (int i = 2 * REG_ENTRIES; i < 2 * c.pn; i++) le[i] = c.pe[i];
+  c.pe = le;
+  c.pcap = LONG_CHAIN;
   c.long_id = id;
   return true;
 }
@@ -130,7 +150,7 @@ __device__ __forceinline__ bool grow_plan(const DevTable& t, Ctx& c) {
 // Room for the next few entries: 0, or the status to give up with (a full
 // scratch plan cannot happen under the cap; no free scratch plan: retry).
 __device__ __forceinline__ int plan_room(const DevTable& t, Ctx& c) {
-  if (c.plan->n < c.plan->cap - 4) return 0;
+  if (c.pn < c.pcap - 4) return 0;
   if (grow_plan(t, c)) return 0;
   return c.long_id >= 0 ? (int)ST_FAILED : (int)ST_CONFLICT;
 }
@@ -141,18 +161,17 @@ __device__ __forceinline__ bool claim(const DevTable& t, Ctx& c, uint32_t bin, u
                                       bool hit, uint64_t content, uint32_t old_r = 0, uint32_t new_r = 0) {
   uint32_t desired = m + (hit ? HIT_ONE : 0u) + (1u << s);
   if (!cas_acquire(t.meta + bin, m, desired)) return false;
-  put_entry(*c.plan, pack_entry(bin, s, kind, hit, old_r, new_r), content);
+  put_entry(c, pack_entry(bin, s, kind, hit, old_r, new_r), content);
   return true;
 }
 
 // Abandon the plan: drop every claim (and hit increment); nothing was written.
 __device__ __forceinline__ void release_all(const DevTable& t, Ctx& c) {
-  Plan& p = *c.plan;
-  for (int i = 0; i < p.n; i++) {
-    uint64_t e = desc_at(p, i);
+  for (int i = 0; i < c.pn; i++) {
+    uint64_t e = desc_at(c, i);
     red_relaxed(t.meta + e_bin(e), 0u - ((1u << e_slot(e)) + (e_hit(e) ? HIT_ONE : 0u)));
   }
-  p.n = 0;
+  c.pn = 0;
 }
 
 // Apply the plan back to front, then release every claim.  Entry 0 of the
@@ -163,23 +182,22 @@ __device__ __forceinline__ void release_all(const DevTable& t, Ctx& c) {
 // duplicate mark or rattle counter of its slot.
 template <int B>
 __device__ __forceinline__ void commit(const DevTable& t, Ctx& c) {
-  Plan& p = *c.plan;
   int n_chain = 0;
-  while (n_chain < p.n && (e_kind(desc_at(p, n_chain)) == K_MOVE || e_kind(desc_at(p, n_chain)) == K_DUPTERM))
+  while (n_chain < c.pn && (e_kind(desc_at(c, n_chain)) == K_MOVE || e_kind(desc_at(c, n_chain)) == K_DUPTERM))
     n_chain++;
   for (int i = n_chain - 1; i >= 0; i--) {
-    uint64_t rec = (i == 0) ? c.krec : content_at(p, i - 1);
-    uint64_t ei = desc_at(p, i);
+    uint64_t rec = (i == 0) ? c.krec : content_at(c, i - 1);
+    uint64_t ei = desc_at(c, i);
     st_slot(t.slots + (uint64_t)e_bin(ei) * B + e_slot(ei), rec);
     if (t.ordered_writes && i > 0) fence_release();  // the copy lands before its source is overwritten
   }
-  for (int i = n_chain; i < p.n; i++) {
-    uint64_t ei = desc_at(p, i);
+  for (int i = n_chain; i < c.pn; i++) {
+    uint64_t ei = desc_at(c, i);
     if (e_kind(ei) == K_GHOST) st_slot(t.slots + (uint64_t)e_bin(ei) * B + e_slot(ei), c.krec);
   }
   fence_release();
-  for (int i = 0; i < p.n; i++) {
-    uint64_t ei = desc_at(p, i);
+  for (int i = 0; i < c.pn; i++) {
+    uint64_t ei = desc_at(c, i);
     uint32_t sl = e_slot(ei);
     uint32_t delta = VER_ONE - (1u << sl);
     if (B == 1) {
@@ -197,18 +215,18 @@ __device__ __forceinline__ void commit(const DevTable& t, Ctx& c) {
 // failure; one reached after detours around claims is retried instead.
 __device__ __forceinline__ bool claims_none_foreign(const Ctx& c) { return !c.foreign; }
 
-__device__ __forceinline__ bool plan_has_bin(const Plan& p, uint32_t bin) {
-  for (int i = 0; i < p.n; i++)
-    if (e_bin(desc_at(p, i)) == bin) return true;
+__device__ __forceinline__ bool plan_has_bin(const Ctx& c, uint32_t bin) {
+  for (int i = 0; i < c.pn; i++)
+    if (e_bin(desc_at(c, i)) == bin) return true;
   return false;
 }
 
 // Every claimed slot of this view belongs to our own plan.
 template <int B>
-__device__ __forceinline__ bool claims_all_ours(const Plan& p, uint32_t bin, uint32_t claimed) {
+__device__ __forceinline__ bool claims_all_ours(const Ctx& c, uint32_t bin, uint32_t claimed) {
   uint32_t ours = 0;
-  for (int i = 0; i < p.n; i++)
-    if (e_bin(desc_at(p, i)) == bin) ours |= 1u << e_slot(desc_at(p, i));
+  for (int i = 0; i < c.pn; i++)
+    if (e_bin(desc_at(c, i)) == bin) ours |= 1u << e_slot(desc_at(c, i));
   return (claimed & ~ours) == 0;
 }
 
@@ -262,12 +280,10 @@ __device__ __forceinline__ int take_dup(const DevTable& t, Ctx& c, uint32_t bin,
     if (!claim_twin<B>(t, c, g, y)) return ST_CONFLICT;
     if (!claim(t, c, bin, v.m, s, K_DUPTERM, hit, g)) return ST_CONFLICT;
     // keep the chain entries contiguous: the twin goes after the terminal
-    Plan& p = *c.plan;
-    uint64_t td = p.e[2 * (p.n - 2)], tc = p.e[2 * (p.n - 2) + 1];
-    p.e[2 * (p.n - 2)] = p.e[2 * (p.n - 1)];
-    p.e[2 * (p.n - 2) + 1] = p.e[2 * (p.n - 1) + 1];
-    p.e[2 * (p.n - 1)] = td;
-    p.e[2 * (p.n - 1) + 1] = tc;
+    const int a = c.pn - 2, b = c.pn - 1;
+    uint64_t td = desc_at(c, a), tc = content_at(c, a);
+    set_entry(c, a, desc_at(c, b), content_at(c, b));
+    set_entry(c, b, td, tc);
   } else {
     if (!claim(t, c, bin, v.m, s, K_DUPTERM, hit, g)) return ST_CONFLICT;
     if (!claim_twin<B>(t, c, g, y)) return ST_CONFLICT;
@@ -355,7 +371,7 @@ __device__ int insert_random2(const DevTable& t, Ctx& c) {
     }
     uint32_t claimed = claimed_mask<B>(vx);
     uint32_t e = FULL & ~claimed & ~(vx.m >> DUP_SHIFT);
-    if (!e) return claims_all_ours<B>(*c.plan, x, claimed) ? ST_FAILED : ST_CONFLICT;
+    if (!e) return claims_all_ours<B>(c, x, claimed) ? ST_FAILED : ST_CONFLICT;
     if (int r0 = plan_room(t, c)) return r0;
     uint64_t r = draw(t, c.key, c.draws++, c.attempt);
     s = nth_bit(e, (uint32_t)(r % __popc(e)));
@@ -415,7 +431,7 @@ __device__ int insert_queue(const DevTable& t, Ctx& c) {
         uint32_t claimed = claimed_mask<B>(vx);
         uint32_t um = FULL & ~claimed & ~(vx.m >> DUP_SHIFT);
         int s = first_from<B>(um, h);
-        if (s < 0) return claims_all_ours<B>(*c.plan, x, claimed) ? ST_FAILED : ST_CONFLICT;
+        if (s < 0) return claims_all_ours<B>(c, x, claimed) ? ST_FAILED : ST_CONFLICT;
         if (c.kicks == t.cap) return ST_FAILED;
         if (int r0 = plan_room(t, c)) return r0;
         if (claim(t, c, x, vx.m, s, K_MOVE, true, slot_of<B>(vx, s))) {
@@ -528,7 +544,7 @@ __device__ inline int insert_random_dary(const DevTable& t, Ctx& c) {
     for (uint32_t i = 0; i < t.d; i++) {
       if (vb[i] == x) continue;  // just claimed by this chain
       if (!claimed_mask<1>(w[i])) { cb[nc] = vb[i]; cv[nc] = w[i]; nc++; }
-      else if (!plan_has_bin(*c.plan, vb[i])) c.foreign = 1;
+      else if (!plan_has_bin(c, vb[i])) c.foreign = 1;
     }
     counted = false;
   }
@@ -554,7 +570,7 @@ __device__ inline int insert_rattle(const DevTable& t, Ctx& c) {
     if (claimed_mask<1>(vx)) {
       // this chain's own bin: skipped, not viewed; another insertion's:
       // viewed and ignored (Sec. 8)
-      if (!plan_has_bin(*c.plan, x)) {
+      if (!plan_has_bin(c, x)) {
         c.viewed++;
         c.foreign = 1;
       }

@@ -15,9 +15,12 @@ __device__ __forceinline__ void flush_counter(unsigned long long* shared_slot, u
   if (x) atomicAdd(shared_slot, x);
 }
 
+// Randomised exponential backoff after a conflict: [w, 2w) ns with w =
+// 64 << attempt, up to about a millisecond, so that long walks that keep
+// meeting each other (small tables with most keys in flight) drift apart.
 __device__ __forceinline__ void backoff(uint32_t attempt, uint32_t key) {
-  uint32_t ns = 64u << (attempt < 6 ? attempt : 6);
-  __nanosleep(ns + (fmix32(key ^ attempt) & 63u));
+  uint32_t w = 64u << (attempt < 14 ? attempt : 14);
+  __nanosleep(w + (fmix32(key ^ attempt) & (w - 1)));
 }
 
 template <int B, int POL, bool GHOST>
@@ -59,7 +62,7 @@ __device__ __forceinline__ int acquire_slab(const DevTable& t) {
 // (up to 3 times): its path depended on the timing of other insertions.
 template <int B, int POL, bool GHOST>
 __device__ __forceinline__ int insert_one(const DevTable& t, Ctx& c, uint8_t* region, uint32_t& aborts,
-                                          Plan local, bool retry_failed = false) {
+                                          uint64_t* local_e, int local_cap, bool retry_failed = false) {
   c.long_id = -1;
   int st;
   uint32_t fails = 0;
@@ -71,8 +74,11 @@ __device__ __forceinline__ int insert_one(const DevTable& t, Ctx& c, uint8_t* re
     c.ghosts_made = 0;
     c.dup_evict = 0;
     c.foreign = 0;
-    c.plan = c.long_id >= 0 ? &c.lp : &local;
-    c.plan->n = 0;
+    if (c.long_id < 0) {
+      c.pe = local_e;
+      c.pcap = local_cap;
+    }
+    c.pn = 0;
     st = attempt_insert<B, POL, GHOST>(t, c, region);
     if (st == ST_OK) {
       commit<B>(t, c);
@@ -133,11 +139,16 @@ __global__ void __launch_bounds__(256) k_insert(DevTable t, const uint32_t* __re
   __syncthreads();
 
   PlanStore<SERIAL ? 1 : MAX_CHAIN> store;
-  Plan local = store.view();
+  uint64_t* local_e = store.e;
+  int local_cap = SERIAL ? 1 : MAX_CHAIN;
   bool usable = true;
   if (SERIAL) {
-    if (s_long >= 0) local = plan_in(t.long_scratch + (uint64_t)s_long * LONG_REGION);
-    else usable = false;
+    if (s_long >= 0) {
+      local_e = reinterpret_cast<uint64_t*>(t.long_scratch + (uint64_t)s_long * LONG_REGION);
+      local_cap = LONG_CHAIN;
+    } else {
+      usable = false;
+    }
   }
   uint8_t* region = s_slab >= 0 ? t.scratch + ((uint64_t)s_slab * SLAB + threadIdx.x) * SEARCH_REGION
                                 : nullptr;
@@ -161,7 +172,7 @@ __global__ void __launch_bounds__(256) k_insert(DevTable t, const uint32_t* __re
     c.krec = ((uint64_t)key << 32) | vals[i];
     c.viewed = 0;
     c.reviews = 0;
-    int st = usable ? insert_one<B, POL, GHOST>(t, c, region, aborts, local, !SERIAL && POL == P_RANDOM)
+    int st = usable ? insert_one<B, POL, GHOST>(t, c, region, aborts, local_e, local_cap, !SERIAL && POL == P_RANDOM)
                     : (int)ST_ABORTED;
     if (st == ST_OK) {
       ok++;
@@ -352,27 +363,37 @@ struct DelPlan {
   int n;
 };
 
+// One delete: find the key in its bins and claim the slots holding it
+// (every copy: a ghost pair has two), clear them, release.  A miss is
+// reported only when the bins were seen unclaimed and unchanged across the
+// read (unchanged_since), so a delete running beside insertions on another
+// stream never misses a key that is being moved.  Slots claimed by a
+// writer are waited out with backoff, at most DELETE_ATTEMPTS times
+// (status 2).
+constexpr int DELETE_ATTEMPTS = 1024;
+
 template <int B>
 __device__ __forceinline__ int delete_one(const DevTable& t, uint32_t key, DelPlan& p, uint32_t& ghost_removed) {
   uint32_t b[4];
   bins_of(t, key, b);
   const uint32_t nb = t.d;
-  for (int attempt = 0; attempt < 16; attempt++) {
+  constexpr uint32_t CLAIM_BITS = (1u << B) - 1;
+  for (int attempt = 0; attempt < DELETE_ATTEMPTS; attempt++) {
     p.n = 0;
     bool conflict = false, any = false;
     int dup_copies = 0;
+    uint32_t seen[4];
     for (uint32_t j = 0; j < nb && !conflict; j++) {
       View<B> v;
       load_view<B>(t, b[j], v);
       uint32_t m = v.m;
+      seen[j] = m;
       uint32_t add = 0;
-      int first = -1;
 #pragma unroll
       for (int s = 0; s < B; s++) {
         if (v.s[s] != EMPTY && key_of(v.s[s]) == key) {
-          if ((m >> s) & 1u) { conflict = true; break; }  // an insertion holds it: no waiting
+          if ((m >> s) & 1u) { conflict = true; break; }  // a writer holds it
           add |= 1u << s;
-          if (first < 0) first = s;
         }
       }
       if (conflict || !add) continue;
@@ -388,13 +409,17 @@ __device__ __forceinline__ int delete_one(const DevTable& t, uint32_t key, DelPl
         }
       }
     }
+    if (!conflict && !any) {
+      if (unchanged_since(t.meta, b, seen, nb, CLAIM_BITS)) return 0;
+      conflict = true;  // a writer was active in the key's bins: look again
+    }
     if (conflict) {
       for (int i = 0; i < p.n; i++) add_relaxed(t.meta + p.bin[i], 0u - (1u << p.slot[i]));
       p.n = 0;
-      __nanosleep(128u << (attempt < 5 ? attempt : 5));
+      uint32_t w = 128u << (attempt < 13 ? attempt : 13);
+      __nanosleep(w + (fmix32(key ^ attempt) & (w - 1)));
       continue;
     }
-    if (!any) return 0;
     for (int i = 0; i < p.n; i++) st_slot(t.slots + (uint64_t)p.bin[i] * B + p.slot[i], EMPTY);
     for (int i = 0; i < p.n; i++) {
       uint32_t delta = VER_ONE - (1u << p.slot[i]);

@@ -161,7 +161,7 @@ int init_table(ck_table* t, void* buf, size_t bytes, bool owns, uint64_t bins, u
 template <int B, int POL, bool GHOST>
 cudaError_t launch_insert_dt(const DevTable& dt, uint32_t block, int sm_count, bool overlap, uint64_t load_base,
                              const uint32_t* keys, const uint32_t* vals, uint64_t n, uint8_t* st, uint32_t* viewed,
-                             bool serial, cudaStream_t s) {
+                             bool serial, cudaStream_t s, uint64_t max_threads = ~0ull) {
   if (serial) {
     k_insert<B, POL, GHOST, true><<<1, 1, 0, s>>>(dt, keys, vals, n, st, viewed, load_base);
     return cudaGetLastError();
@@ -180,6 +180,8 @@ cudaError_t launch_insert_dt(const DevTable& dt, uint32_t block, int sm_count, b
   uint64_t grid = (n + block - 1) / block;
   uint64_t resident = (uint64_t)cached_per_sm * sm_count;
   if (grid > resident) grid = resident;
+  uint64_t by_threads = max_threads / block;  // insertions in flight at once
+  if (grid > by_threads) grid = by_threads > 0 ? by_threads : 1;
   if (dt.scratch) {
     uint64_t cap_blocks = dt.n_searchers / SLAB;
     if (grid > cap_blocks) grid = cap_blocks;
@@ -239,22 +241,32 @@ unsigned grid_for(uint64_t n, uint32_t block) {
 // Device view of a handle, for the other translation units of the library.
 const ck::DevTable* ck_internal_devtable(const ck_table* t) { return &t->dt; }
 
+// The stream that host-side reads of the table (stats, export) wait for;
+// the serving loop hands it back when it lets go of the table.
+void* ck_internal_swap_last(ck_table* t, void* s) {
+  void* old = t->last;
+  t->last = S(s);
+  return old;
+}
+
 // The single-table insert launch for a bare device view (the batched form's
-// one-launch-per-table reference path): concurrent mode, overlapping launches.
+// one-launch-per-table reference path): concurrent mode, overlapping launches,
+// at most max_threads insertions in flight.
 int ck_internal_launch_insert(const DevTable& dt, uint32_t block, int sm_count, const uint32_t* keys,
-                              const uint32_t* vals, uint64_t n, uint8_t* status, cudaStream_t s) {
+                              const uint32_t* vals, uint64_t n, uint8_t* status, cudaStream_t s,
+                              uint64_t max_threads) {
   cudaError_t e = cudaErrorInvalidValue;
   bool g = dt.ghost != 0;
   if (dt.B == 4) {
-    if (dt.policy == CK_QUEUE) e = g ? launch_insert_dt<4, P_QUEUE, true>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s)
-                                     : launch_insert_dt<4, P_QUEUE, false>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s);
-    else if (dt.policy == CK_RANDOM) e = g ? launch_insert_dt<4, P_RANDOM, true>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s)
-                                           : launch_insert_dt<4, P_RANDOM, false>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s);
+    if (dt.policy == CK_QUEUE) e = g ? launch_insert_dt<4, P_QUEUE, true>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s, max_threads)
+                                     : launch_insert_dt<4, P_QUEUE, false>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s, max_threads);
+    else if (dt.policy == CK_RANDOM) e = g ? launch_insert_dt<4, P_RANDOM, true>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s, max_threads)
+                                           : launch_insert_dt<4, P_RANDOM, false>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s, max_threads);
   } else if (dt.B == 8) {
-    if (dt.policy == CK_QUEUE) e = g ? launch_insert_dt<8, P_QUEUE, true>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s)
-                                     : launch_insert_dt<8, P_QUEUE, false>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s);
-    else if (dt.policy == CK_RANDOM) e = g ? launch_insert_dt<8, P_RANDOM, true>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s)
-                                           : launch_insert_dt<8, P_RANDOM, false>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s);
+    if (dt.policy == CK_QUEUE) e = g ? launch_insert_dt<8, P_QUEUE, true>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s, max_threads)
+                                     : launch_insert_dt<8, P_QUEUE, false>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s, max_threads);
+    else if (dt.policy == CK_RANDOM) e = g ? launch_insert_dt<8, P_RANDOM, true>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s, max_threads)
+                                           : launch_insert_dt<8, P_RANDOM, false>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s, max_threads);
   }
   return e == cudaSuccess ? CK_OK : CK_ECUDA;
 }

@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(128) k_insert_noalloc(DevTable t, uint8_t* scr
     if (key != RESERVED_KEY) {
       c.key = key;
       c.krec = ((uint64_t)key << 32) | vals[i];
-      st = insert_one<B, POL, GHOST>(t, c, region, aborts, store.view());
+      st = insert_one<B, POL, GHOST>(t, c, region, aborts, store.e, MAX_CHAIN);
     }
     if (status) status[i] = (uint8_t)st;
     if (st != ST_INVALID) {

@@ -165,29 +165,27 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
     // path root -> ... -> (g, s): depth entries in chain order
     uint32_t depth = 1;
     for (uint32_t q = g; G[q].parent != ~0u; q = G[q].parent >> 3) depth++;
-    if ((int)depth + 4 > c.plan->cap) return ST_LONG;
-    Plan& p = *c.plan;
+    if ((int)depth + 4 > c.pcap) return ST_LONG;
     {
       // entries in chain order; the group index rides in the content word
       // until the slot is claimed
       uint32_t q = g, qs = s;
       for (int i = (int)depth - 1; i >= 0; i--) {
-        p.e[2 * i] = pack_entry(G[q].bin, (int)qs, K_MOVE, false, 0, 0);
-        p.e[2 * i + 1] = q;
+        set_entry(c, i, pack_entry(G[q].bin, (int)qs, K_MOVE, false, 0, 0), q);
         uint32_t par = G[q].parent;
         if (par != ~0u) { qs = par & 7u; q = par >> 3; }
       }
     }
     // claim the path in chain order; each CAS checks its bin is as viewed,
     // so the record read after the claim is the one the search saw
-    p.n = 0;
+    c.pn = 0;
     for (uint32_t i = 0; i < depth; i++) {
-      Group gq = G[(uint32_t)p.e[2 * i + 1]];
-      uint32_t sl = e_slot(p.e[2 * i]);
+      Group gq = G[(uint32_t)content_at(c, (int)i)];
+      uint32_t sl = e_slot(desc_at(c, (int)i));
       if (gq.stale) return ST_CONFLICT;
       if (!cas_acquire(t.meta + gq.bin, gq.meta, gq.meta + (1u << sl))) return ST_CONFLICT;
-      p.n = (int)i + 1;
-      p.e[2 * i + 1] = ld_slot(t.slots + (uint64_t)gq.bin * B + sl);
+      c.pn = (int)i + 1;
+      set_content(c, (int)i, ld_slot(t.slots + (uint64_t)gq.bin * B + sl));
     }
     c.kicks = depth;
     if (isdup) return take_dup<B>(t, c, y, vy, term, false);

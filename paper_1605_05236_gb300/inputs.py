@@ -174,3 +174,62 @@ def multi_keys(bins, slots, load: float, seed0: int = 8):
         keys[off:off + int(n)] = k
         off += int(n)
     return keys, values_for(keys), n_keys
+
+
+def serving_trace(prefill_keys: np.ndarray, n_req: int, mix: tuple, seed: int = 11,
+                  rate_per_ms: float = 20000.0, max_log2: int = 16, hit_fraction: float = 0.5):
+    """A request trace for the serving loop.
+
+    Arrivals: a Poisson process of `rate_per_ms` requests per millisecond
+    (exponential gaps from the stream of seed+1).  Sizes: floor(2^(max_log2*u))
+    keys, u uniform (log-uniform 1 .. 2^max_log2; stream seed+2).  Kinds:
+    lookup / insert / delete with probabilities `mix` (stream seed+3).
+    Keys are drawn so every result is fixed by the trace alone, whatever
+    runs concurrently: lookups take present keys from the first half of the
+    prefilled set (never deleted) and absent keys never inserted; inserts
+    take fresh keys; deletes take keys of the second half of the prefilled
+    set, each once.
+
+    Returns dict(op, n_keys, key_off, arrive_ns, keys, vals, expect) with
+    expect = the per-key result (lookups: 1 present / 0 absent; inserts and
+    deletes: 1)."""
+    out = splitmix64_stream(seed + 1, 0, n_req)
+    u = (out >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+    gaps = -np.log1p(-u) / rate_per_ms * 1e6
+    arrive = np.cumsum(gaps).astype(np.int64)
+    arrive -= arrive[0]
+    u2 = (splitmix64_stream(seed + 2, 0, n_req) >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+    n_keys = np.maximum(1, np.floor(2.0 ** (max_log2 * u2))).astype(np.uint64)
+    u3 = (splitmix64_stream(seed + 3, 0, n_req) >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+    cum = np.cumsum(mix) / np.sum(mix)
+    op = np.searchsorted(cum, u3, side="right").astype(np.uint32)
+    op = np.minimum(op, 2)
+    half = len(prefill_keys) // 2
+    stable, deletable = prefill_keys[:half], prefill_keys[half:]
+    n_look = int(n_keys[op == 0].sum())
+    n_ins = int(n_keys[op == 1].sum())
+    n_del = int(n_keys[op == 2].sum())
+    if n_del > len(deletable):
+        raise ValueError("trace deletes more keys than the prefilled set can give")
+    n_hit = int(round(n_look * hit_fraction))
+    fresh, _ = distinct_keys(n_ins + (n_look - n_hit), seed + 4, exclude=prefill_keys)
+    ins_keys, absent = fresh[:n_ins], fresh[n_ins:]
+    present = stable[permutation(len(stable), seed + 5, n_hit)]
+    look = np.concatenate([present, absent])
+    look_exp = np.concatenate([np.ones(n_hit, np.uint8), np.zeros(n_look - n_hit, np.uint8)])
+    order = permutation(n_look, seed + 6)
+    look, look_exp = look[order], look_exp[order]
+    dele = deletable[permutation(len(deletable), seed + 7, n_del)]
+    keys = np.empty(int(n_keys.sum()), dtype=np.uint32)
+    expect = np.ones(len(keys), dtype=np.uint8)
+    key_off = np.concatenate([[0], np.cumsum(n_keys)[:-1]]).astype(np.uint64)
+    pos = [0, 0, 0]
+    for i in range(n_req):
+        o, n, off = int(op[i]), int(n_keys[i]), int(key_off[i])
+        src = (look, ins_keys, dele)[o]
+        keys[off:off + n] = src[pos[o]:pos[o] + n]
+        if o == 0:
+            expect[off:off + n] = look_exp[pos[o]:pos[o] + n]
+        pos[o] += n
+    return {"op": op, "n_keys": n_keys, "key_off": key_off, "arrive_ns": arrive, "keys": keys,
+            "vals": values_for(keys), "expect": expect}

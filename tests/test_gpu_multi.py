@@ -1,0 +1,69 @@
+"""The batched form (one persistent launch over many tables) against the
+one-launch-per-table path and the serial oracle: every table's key->value
+map is the same, and every key is found."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1605_05236_gb300 import ck, inputs
+from paper_1605_05236_gb300 import multi as M
+from table_checks import check_table
+
+pytestmark = pytest.mark.gpu
+
+
+def small_workload(n_tables=64, seed=7):
+    bins, slots = inputs.multi_shapes(n_tables, seed=seed, lo_log2=8, hi_log2=12)
+    keys, vals, n_keys = inputs.multi_keys(bins, slots, 0.95)
+    return bins, slots, keys, vals, n_keys
+
+
+@pytest.mark.parametrize("policy", [ck.QUEUE, ck.RANDOM, ck.QUEUE | ck.GHOST])
+@pytest.mark.parametrize("tile", [256, 4096])
+def test_batched_equals_per_table_and_oracle(policy, tile):
+    bins, slots, keys, vals, n_keys = small_workload()
+    kt, vt = ck.as_u32_tensor(keys), ck.as_u32_tensor(vals)
+    a = M.MultiTable(bins, slots, n_keys, policy, seed=5)
+    b = M.MultiTable(bins, slots, n_keys, policy, seed=5)
+    a.set_param(M.MULTI_TILE, tile)
+    sa = torch.empty(len(keys), dtype=torch.uint8, device="cuda")
+    sb = torch.empty(len(keys), dtype=torch.uint8, device="cuda")
+    a.insert(kt, vt, sa)
+    b.insert(kt, vt, sb, per_table=True)
+    torch.cuda.synchronize()
+    assert bool((sa == 0).all()) and bool((sb == 0).all())
+    off = 0
+    for i in range(len(bins)):
+        n = int(n_keys[i])
+        want = {int(k): int(v) for k, v in zip(keys[off:off + n], vals[off:off + n])}
+        ca, cb = a.contents(i), b.contents(i)
+        assert ca == want and cb == want, i
+        if i < 8:  # a few tables against the serial oracle
+            ref = oracle.OracleTable(int(bins[i]), int(slots[i]), 2, policy, rng_seed=5 + i)
+            assert (ref.insert(keys[off:off + n], vals[off:off + n]) == 0).all()
+            assert ref.contents() == want
+        off += n
+    s = a.stats()
+    assert s["size"] == len(keys) and s["inserts_ok"] == len(keys)
+    tab = torch.from_numpy(np.repeat(np.arange(len(bins), dtype=np.int32), n_keys.astype(np.int64))).cuda()
+    v, f = a.lookup(tab, kt)
+    assert bool((f == 1).all()) and torch.equal(v, vt)
+
+
+def test_batched_invariants_and_clear():
+    bins, slots, keys, vals, n_keys = small_workload(16, seed=9)
+    kt, vt = ck.as_u32_tensor(keys), ck.as_u32_tensor(vals)
+    m = M.MultiTable(bins, slots, n_keys, ck.QUEUE, seed=1)
+    for _ in range(2):  # refill after clear
+        m.clear()
+        m.insert(kt, vt)
+        torch.cuda.synchronize()
+        assert m.stats()["size"] == len(keys)
+    for i in range(len(bins)):
+        slots_i = np.zeros(int(bins[i]) * int(slots[i]), dtype=np.uint64)
+        import ctypes
+        M._lib().ck_multi_export(m._h, i, slots_i.ctypes.data_as(ctypes.c_void_p), None)
+        meta = np.zeros(int(bins[i]), dtype=np.uint32)
+        M._lib().ck_multi_export(m._h, i, None, meta.ctypes.data_as(ctypes.c_void_p))
+        check_table(slots_i, meta, int(bins[i]), int(slots[i]), 2)
