@@ -198,11 +198,12 @@ __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
 
 // A read of a bin's slots that saw no claim bit in the bin's metadata word,
 // and finds the word unchanged when it is read again after the slots, saw
-// no writer: every slot write happens under a claim, and every release
-// advances the bin's version.  This is how a miss is proven while
-// insertions run (a key moving between its own bins is written to the new
-// bin before it leaves the old one, but two separate reads can still fall
-// on either side of the move).
+// no key move: every move (a chain step, a delete) happens under a claim,
+// and every release advances the bin's version.  The one write without a
+// claim, a new key taking a free slot, adds a key and moves none.  This is
+// how a miss is proven while insertions run (a key moving between its own
+// bins is written to the new bin before it leaves the old one, but two
+// separate reads can still fall on either side of the move).
 __device__ __forceinline__ bool unchanged_since(const uint32_t* meta, const uint32_t* bins, const uint32_t* seen,
                                                 uint32_t nb, uint32_t claim_bits) {
   fence_acquire();
@@ -227,6 +228,16 @@ __device__ __forceinline__ uint32_t add_release(uint32_t* p, uint32_t delta) {
 }
 
 // Fire-and-forget atomic add (no value returned).
+// 64-bit compare-and-swap of one slot (relaxed): the unclaimed placement
+// of a new key into a free slot, and a chain's write of its terminal free
+// slot, both of which must not overwrite a key another thread placed there.
+__device__ __forceinline__ bool cas_slot(uint64_t* p, uint64_t expected, uint64_t desired) {
+  unsigned long long old;
+  asm volatile("atom.relaxed.gpu.global.cas.b64 %0, [%1], %2, %3;"
+               : "=l"(old) : "l"(p), "l"(expected), "l"(desired) : "memory");
+  return old == expected;
+}
+
 __device__ __forceinline__ void red_relaxed(uint32_t* p, uint32_t delta) {
   asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" :: "l"(p), "r"(delta) : "memory");
 }
@@ -253,6 +264,48 @@ __device__ __forceinline__ void load_view(const DevTable& t, uint32_t bin, View<
 #pragma unroll
     for (int q = 0; q < B; q += 4) ld_bin4(p + q, v.s + q);
   }
+}
+
+// Views of a key's two bins with one wait: both metadata words (relaxed),
+// one acquire fence, then both bins' slots, so each view's slots are read
+// after its metadata word (what load_view's acquire gives) at the cost of
+// two round trips instead of three.
+#ifndef CK_VIEW2
+#define CK_VIEW2 1
+#endif
+template <int B>
+__device__ __forceinline__ void load_slots(const DevTable& t, uint32_t bin, View<B>& v) {
+  const uint64_t* p = t.slots + (uint64_t)bin * B;
+  if constexpr (B == 1) {
+    v.s[0] = ld_slot(p);
+  } else {
+#pragma unroll
+    for (int q = 0; q < B; q += 4) ld_bin4(p + q, v.s + q);
+  }
+}
+
+// A view without ordering between the metadata word and the slots, for a
+// placement into a free slot (validated by the slot's own compare-and-swap).
+// Before a claim is taken on it, the slots are read again after an acquire
+// fence (reread_slots), which restores load_view's order.
+template <int B>
+__device__ __forceinline__ void load_view_fast(const DevTable& t, uint32_t bin, View<B>& v) {
+  v.m = ld_relaxed(t.meta + bin);
+  load_slots<B>(t, bin, v);
+}
+
+template <int B>
+__device__ __forceinline__ void load_view2(const DevTable& t, uint32_t b0, uint32_t b1, View<B>& v0, View<B>& v1) {
+#if CK_VIEW2
+  v0.m = ld_relaxed(t.meta + b0);
+  v1.m = ld_relaxed(t.meta + b1);
+  fence_acquire();
+  load_slots<B>(t, b0, v0);
+  load_slots<B>(t, b1, v1);
+#else
+  load_view<B>(t, b0, v0);
+  load_view<B>(t, b1, v1);
+#endif
 }
 
 // Slot s of a view, s known only at run time: a chain of selects keeps the

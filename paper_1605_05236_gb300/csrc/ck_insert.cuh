@@ -165,6 +165,24 @@ __device__ __forceinline__ bool claim(const DevTable& t, Ctx& c, uint32_t bin, u
   return true;
 }
 
+#ifndef CK_DIRECT
+#define CK_DIRECT 1
+#endif
+
+// A new key straight into free slot s of `bin` (tables without ghosts):
+// one 64-bit compare-and-swap of the slot from empty to the record, then a
+// relaxed add that advances the bin's version (and, for queue-kicking, its
+// hit counter).  No claim is taken: the key moves nothing, and a chain that
+// had claimed this slot as its terminal finds it taken when it commits and
+// starts again.  With one insertion in flight the slot and the metadata
+// word end exactly as a claim and its release would leave them.
+template <int B>
+__device__ __forceinline__ bool place_direct(const DevTable& t, Ctx& c, uint32_t bin, int s, bool hit) {
+  if (!cas_slot(t.slots + (uint64_t)bin * B + s, EMPTY, c.krec)) return false;
+  red_relaxed(t.meta + bin, VER_ONE + (hit ? HIT_ONE : 0u));
+  return true;
+}
+
 // Abandon the plan: drop every claim (and hit increment); nothing was written.
 __device__ __forceinline__ void release_all(const DevTable& t, Ctx& c) {
   for (int i = 0; i < c.pn; i++) {
@@ -180,15 +198,25 @@ __device__ __forceinline__ void release_all(const DevTable& t, Ctx& c) {
 // never absent for a concurrent reader (Sec. 8); one fence then orders all
 // stores before the relaxed releases, each of which also moves the version,
 // duplicate mark or rattle counter of its slot.
+// The chain's first write, to its terminal, is a compare-and-swap when the
+// terminal is a free slot (a new key may have taken it without a claim); if
+// that fails nothing has been written, and the caller drops the claims and
+// starts again (false).
 template <int B>
-__device__ __forceinline__ void commit(const DevTable& t, Ctx& c) {
+__device__ __forceinline__ bool commit(const DevTable& t, Ctx& c) {
+  if (c.pn == 0) return true;  // placed directly (place_direct)
   int n_chain = 0;
   while (n_chain < c.pn && (e_kind(desc_at(c, n_chain)) == K_MOVE || e_kind(desc_at(c, n_chain)) == K_DUPTERM))
     n_chain++;
   for (int i = n_chain - 1; i >= 0; i--) {
     uint64_t rec = (i == 0) ? c.krec : content_at(c, i - 1);
     uint64_t ei = desc_at(c, i);
-    st_slot(t.slots + (uint64_t)e_bin(ei) * B + e_slot(ei), rec);
+    uint64_t* p = t.slots + (uint64_t)e_bin(ei) * B + e_slot(ei);
+    if (i == n_chain - 1 && e_kind(ei) == K_MOVE && content_at(c, i) == EMPTY) {
+      if (!cas_slot(p, EMPTY, rec)) return false;
+    } else {
+      st_slot(p, rec);
+    }
     if (t.ordered_writes && i > 0) fence_release();  // the copy lands before its source is overwritten
   }
   for (int i = n_chain; i < c.pn; i++) {
@@ -209,6 +237,7 @@ __device__ __forceinline__ void commit(const DevTable& t, Ctx& c) {
     }
     red_relaxed(t.meta + e_bin(ei), delta);
   }
+  return true;
 }
 
 // A cap reached without meeting another insertion's claim is a genuine
@@ -317,7 +346,7 @@ __device__ int insert_random2(const DevTable& t, Ctx& c) {
   uint32_t b0, b1;
   bins2(t, c.key, b0, b1);
   View<B> v0, v1;
-  if (!GHOST) {
+  if (!CK_DIRECT && !GHOST) {
     load_view<B>(t, b0, v0);
     c.viewed++;
     int s = lowest(free_mask<B>(v0));
@@ -326,9 +355,22 @@ __device__ int insert_random2(const DevTable& t, Ctx& c) {
     c.viewed++;
     s = lowest(free_mask<B>(v1));
     if (s >= 0) return take_free<B>(t, c, b1, v1, s, false);
+  } else if (!GHOST) {
+    // the first free slot of b0, then of b1, placed by a compare-and-swap
+    // of the slot on unordered views
+    load_view_fast<B>(t, b0, v0);
+    c.viewed++;
+    int s = lowest(free_mask<B>(v0));
+    if (s >= 0) return place_direct<B>(t, c, b0, s, false) ? (int)ST_OK : (int)ST_CONFLICT;
+    load_view_fast<B>(t, b1, v1);
+    c.viewed++;
+    s = lowest(free_mask<B>(v1));
+    if (s >= 0) return place_direct<B>(t, c, b1, s, false) ? (int)ST_OK : (int)ST_CONFLICT;
+    fence_acquire();  // both metadata words before both bins' slots
+    load_slots<B>(t, b0, v0);
+    load_slots<B>(t, b1, v1);
   } else {
-    load_view<B>(t, b0, v0);
-    load_view<B>(t, b1, v1);
+    load_view2<B>(t, b0, b1, v0, v1);
     c.viewed += 2;
     uint32_t f0 = free_mask<B>(v0), f1 = free_mask<B>(v1);
     if (f0 && f1) {
@@ -384,15 +426,36 @@ __device__ int insert_random2(const DevTable& t, Ctx& c) {
 // The claim of a slot and the increment of the bin's hit counter are one
 // compare-and-swap, the GPU form of the paper's fetch-and-add scheduling:
 // B insertions arriving at one bin are handed B different slots.
+#ifndef CK_WALK_PREFETCH
+#define CK_WALK_PREFETCH 1
+#endif
+
 template <int B, bool GHOST>
 __device__ int insert_queue(const DevTable& t, Ctx& c) {
   constexpr uint32_t FULL = (1u << B) - 1;
   uint32_t b0, b1;
   bins2(t, c.key, b0, b1);
   View<B> v0, v1;
-  load_view<B>(t, b0, v0);
-  load_view<B>(t, b1, v1);
-  c.viewed += 2;
+  if (CK_DIRECT && !GHOST) {
+    // the common case first: a free slot in the less full bin, placed by a
+    // compare-and-swap of the slot on an unordered view
+    load_view_fast<B>(t, b0, v0);
+    load_view_fast<B>(t, b1, v1);
+    c.viewed += 2;
+    uint32_t g0 = free_mask<B>(v0), g1 = free_mask<B>(v1);
+    if (g0 | g1) {
+      bool first = __popc(g0) >= __popc(g1);
+      uint32_t x = first ? b0 : b1;
+      int s = first_from<B>(first ? g0 : g1, hit_of(first ? v0.m : v1.m) % B);
+      return place_direct<B>(t, c, x, s, true) ? (int)ST_OK : (int)ST_CONFLICT;
+    }
+    fence_acquire();  // both metadata words before both bins' slots
+    load_slots<B>(t, b0, v0);
+    load_slots<B>(t, b1, v1);
+  } else {
+    load_view2<B>(t, b0, b1, v0, v1);
+    c.viewed += 2;
+  }
   uint32_t fm0 = free_mask<B>(v0), fm1 = free_mask<B>(v1);
   int f0 = __popc(fm0), f1 = __popc(fm1);
   if (GHOST && f0 > 0 && f1 > 0) {
@@ -430,13 +493,30 @@ __device__ int insert_queue(const DevTable& t, Ctx& c) {
       } else {
         uint32_t claimed = claimed_mask<B>(vx);
         uint32_t um = FULL & ~claimed & ~(vx.m >> DUP_SHIFT);
+        // a detour around another insertion's claim: reaching the cap after
+        // one is not the serial algorithm's failure
+        if (claimed && !c.foreign && !claims_all_ours<B>(c, x, claimed)) c.foreign = 1;
         int s = first_from<B>(um, h);
-        if (s < 0) return claims_all_ours<B>(c, x, claimed) ? ST_FAILED : ST_CONFLICT;
-        if (c.kicks == t.cap) return ST_FAILED;
+        if (s < 0) return c.foreign ? ST_CONFLICT : ST_FAILED;
+        if (c.kicks == t.cap) return c.foreign ? ST_CONFLICT : ST_FAILED;
         if (int r0 = plan_room(t, c)) return r0;
-        if (claim(t, c, x, vx.m, s, K_MOVE, true, slot_of<B>(vx, s))) {
+        const uint64_t victim = slot_of<B>(vx, s);
+        const uint32_t xn = other_bin2(t, victim, x);
+#if CK_WALK_PREFETCH
+        // the next bin's metadata word travels with the claim; a fence
+        // then orders it before that bin's slots
+        const uint32_t mn = ld_relaxed(t.meta + xn);
+#endif
+        if (claim(t, c, x, vx.m, s, K_MOVE, true, victim)) {
           c.kicks++;
-          x = other_bin2(t, slot_of<B>(vx, s), x);
+          x = xn;
+#if CK_WALK_PREFETCH
+          vx.m = mn;
+          fence_acquire();
+          load_slots<B>(t, x, vx);
+#else
+          load_view<B>(t, x, vx);
+#endif
           break;
         }
       }
@@ -445,7 +525,6 @@ __device__ int insert_queue(const DevTable& t, Ctx& c) {
       c.viewed++;
       c.reviews++;
     }
-    load_view<B>(t, x, vx);
     c.viewed++;
   }
 }

@@ -81,8 +81,8 @@ __device__ __forceinline__ int insert_one(const DevTable& t, Ctx& c, uint8_t* re
     c.pn = 0;
     st = attempt_insert<B, POL, GHOST>(t, c, region);
     if (st == ST_OK) {
-      commit<B>(t, c);
-      break;
+      if (commit<B>(t, c)) break;
+      st = ST_CONFLICT;  // the terminal free slot was taken: nothing written
     }
     release_all(t, c);
     if (st == ST_LONG) {  // a search path longer than the local plan
@@ -113,8 +113,14 @@ __device__ __forceinline__ int insert_one(const DevTable& t, Ctx& c, uint8_t* re
 // after its predecessor.  Insertions of distinct absent keys commute under
 // the claim protocol, so the overlap changes no result.  `load_base` is the
 // number of keys the table held before this batch (for the histogram).
+#if defined(CK_INSERT_MIN_BLOCKS) && CK_INSERT_MIN_BLOCKS > 0
+#define CK_INSERT_BOUNDS __launch_bounds__(256, CK_INSERT_MIN_BLOCKS)
+#else
+#define CK_INSERT_BOUNDS __launch_bounds__(256)
+#endif
+
 template <int B, int POL, bool GHOST, bool SERIAL>
-__global__ void __launch_bounds__(256) k_insert(DevTable t, const uint32_t* __restrict__ keys,
+__global__ void CK_INSERT_BOUNDS k_insert(DevTable t, const uint32_t* __restrict__ keys,
                                                 const uint32_t* __restrict__ vals, uint64_t n,
                                                 uint8_t* __restrict__ status,
                                                 uint32_t* __restrict__ viewed_out, uint64_t load_base) {
@@ -155,8 +161,10 @@ __global__ void __launch_bounds__(256) k_insert(DevTable t, const uint32_t* __re
   if (t.scratch && !region) usable = false;
   const unsigned long long size_base = load_base;
 
-  unsigned long long ok = 0, failed = 0, aborted = 0, viewed = 0, kicks = 0, ghosts = 0, dupev = 0;
-  unsigned long long reviews = 0, viewed_all = 0;
+  // per-thread tallies of one launch (32-bit: a thread handles far fewer
+  // than 2^32 keys or bin views in one launch), flushed into 64-bit counters
+  uint32_t ok = 0, failed = 0, aborted = 0, viewed = 0, kicks = 0, ghosts = 0, dupev = 0;
+  uint32_t reviews = 0, viewed_all = 0;
   uint32_t aborts = 0, chain_max = 0;
   for (;;) {
     uint64_t i = atomicAdd(&s_next, 1ull);
@@ -271,6 +279,10 @@ __device__ __forceinline__ void load_bin_nc(const DevTable& t, uint32_t bin, uin
 
 // Two-choice lookup: both bins are fetched at once (two independent sector
 // loads in flight per key).
+#ifndef CK_LOOKUP_EARLY
+#define CK_LOOKUP_EARLY 0
+#endif
+
 template <int B>
 __global__ void __launch_bounds__(256) k_lookup2(DevTable t, const uint32_t* __restrict__ keys, uint64_t n,
                                                  uint32_t* __restrict__ vals_out,
@@ -288,10 +300,21 @@ __global__ void __launch_bounds__(256) k_lookup2(DevTable t, const uint32_t* __r
       uint32_t b0, b1;
       bins2(t, key, b0, b1);
       uint64_t s0[B], s1[B];
+#if CK_LOOKUP_EARLY
+      // second bin only when the first does not hold the key: fewer bytes
+      // for hits in b0, a second round trip for the rest
+      load_bin_nc<B>(t, b0, s0);
+      f = match_bin<B>(s0, key, val);
+      if (!f) {
+        load_bin_nc<B>(t, b1, s1);
+        f = match_bin<B>(s1, key, val);
+      }
+#else
       load_bin_nc<B>(t, b0, s0);
       load_bin_nc<B>(t, b1, s1);
       f = match_bin<B>(s0, key, val);
       if (!f) f = match_bin<B>(s1, key, val);
+#endif
     }
     hits += f;
     cnt++;

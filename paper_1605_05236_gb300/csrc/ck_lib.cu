@@ -63,11 +63,15 @@ uint32_t searchers_for(uint64_t bins) {
 }
 
 // scratch plans for chains longer than a thread's local plan (and for the
-// serial replay): a few per table, more for large tables
-uint32_t long_plans_for(uint64_t bins) {
+// serial replay): a few per table, more for large tables.  d-ary random
+// kicking walks past the local plan often near its load limits (chains of
+// ~1,500-2,300 at 0.90 / 0.96), so it gets up to 4096 plans, enough for the
+// long walks a full GPU has in flight at once.
+uint32_t long_plans_for(uint64_t bins, uint32_t B, uint32_t policy) {
+  const uint64_t most = (B == 1 && (policy & 0xFF) == CK_RANDOM) ? 4096 : 1024;
   uint64_t k = bins / 4096;
   if (k < 8) k = 8;
-  if (k > 1024) k = 1024;
+  if (k > most) k = most;
   return (uint32_t)k;
 }
 
@@ -84,11 +88,11 @@ Layout layout(uint64_t bins, uint32_t B, uint32_t policy) {
   L.counters = off;
   off = align_up(off + (C_N + 2 * HIST_BUCKETS) * sizeof(uint64_t));
   L.busy = off;
-  off = align_up(off + long_plans_for(bins) * sizeof(uint32_t));
+  off = align_up(off + long_plans_for(bins, B, policy) * sizeof(uint32_t));
   L.slab_busy = off;
   if (is_search(policy)) off = align_up(off + (searchers_for(bins) / SLAB) * sizeof(uint32_t));
   L.long_plans = off;
-  off = align_up(off + (size_t)long_plans_for(bins) * LONG_REGION);
+  off = align_up(off + (size_t)long_plans_for(bins, B, policy) * LONG_REGION);
   L.scratch = off;
   if (is_search(policy)) off = align_up(off + (size_t)searchers_for(bins) * SEARCH_REGION);
   L.total = off;
@@ -124,7 +128,7 @@ int init_table(ck_table* t, void* buf, size_t bytes, bool owns, uint64_t bins, u
   dt.long_scratch = base + L.long_plans;
   dt.long_busy = reinterpret_cast<uint32_t*>(base + L.busy);
   dt.slab_busy = is_search(policy) ? reinterpret_cast<uint32_t*>(base + L.slab_busy) : nullptr;
-  dt.n_long = long_plans_for(bins);
+  dt.n_long = long_plans_for(bins, B, policy);
   dt.n_bins = bins;
   dt.total_slots = bins * B;
   dt.rng_seed = seed;

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(256) k_multi_insert(const DevTable* __restrict
     if (s_tile >= n_tiles) break;
     const DevTable t = tables[s_table];
     const unsigned long long hi = s_hi;
-    unsigned long long ok = 0, failed = 0, aborted = 0, viewed = 0, viewed_all = 0, kicks = 0;
+    uint32_t ok = 0, failed = 0, aborted = 0, viewed = 0, viewed_all = 0, kicks = 0;  // per tile
     uint32_t aborts = 0, chain_max = 0, ghosts = 0, dupev = 0;
     for (;;) {
       unsigned long long i = atomicAdd(&s_next, 1ull);

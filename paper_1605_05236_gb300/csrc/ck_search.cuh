@@ -65,9 +65,22 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
   uint32_t b0, b1;
   bins2(t, c.key, b0, b1);
   View<B> v0, v1;
-  load_view<B>(t, b0, v0);
-  load_view<B>(t, b1, v1);
-  c.viewed += 2;
+  if (CK_DIRECT && !GHOST) {
+    // a free slot of b0, then of b1, placed by a compare-and-swap of the
+    // slot on unordered views; the search needs ordered ones
+    load_view_fast<B>(t, b0, v0);
+    load_view_fast<B>(t, b1, v1);
+    c.viewed += 2;
+    uint32_t g0 = free_mask<B>(v0), g1 = free_mask<B>(v1);
+    if (g0) return place_direct<B>(t, c, b0, lowest(g0), false) ? (int)ST_OK : (int)ST_CONFLICT;
+    if (g1) return place_direct<B>(t, c, b1, lowest(g1), false) ? (int)ST_OK : (int)ST_CONFLICT;
+    fence_acquire();
+    load_slots<B>(t, b0, v0);
+    load_slots<B>(t, b1, v1);
+  } else {
+    load_view2<B>(t, b0, b1, v0, v1);
+    c.viewed += 2;
+  }
   uint32_t f0 = free_mask<B>(v0), f1 = free_mask<B>(v1);
   if (GHOST) {
     if (f0 && f1) {
