@@ -205,6 +205,19 @@ def batch_profile(torch, ck, table, kt, vt, st, stream):
             "launch_ms_at_load": {"%.3f" % (min(n, i * BATCH) / (BINS * B)): round(per[i], 4) for i in idx}}
 
 
+def chain_summary(hist):
+    """Median, 99th percentile and mean chain length (kick-outs) from a
+    ck_chain_histogram (bucket lower bounds beyond 31)."""
+    hist = np.asarray(hist, dtype=np.float64)
+    lo = np.array([i if i < 32 else 2 ** (i - 27) for i in range(len(hist))], dtype=np.float64)
+    total = hist.sum()
+    if total == 0:
+        return {}
+    cdf = np.cumsum(hist) / total
+    return {"p50": int(lo[np.searchsorted(cdf, 0.5)]), "p99": int(lo[np.searchsorted(cdf, 0.99)]),
+            "p999": int(lo[np.searchsorted(cdf, 0.999)]), "zero_kick_share": round(float(hist[0] / total), 4)}
+
+
 def policy_fills(torch, ck, stream, base_keys):
     """One fill per policy on the same shapes (the policy rows of the path)."""
     from paper_1605_05236_gb300 import inputs
@@ -214,7 +227,8 @@ def policy_fills(torch, ck, stream, base_keys):
     st = torch.empty(len(keys), dtype=torch.uint8, device="cuda")
     for name, pol in (("random", ck.RANDOM), ("bfs", ck.BFS), ("sorted", ck.SORTED), ("queue", ck.QUEUE),
                       ("random+ghost", ck.RANDOM | ck.GHOST), ("bfs+ghost", ck.BFS | ck.GHOST),
-                      ("sorted+ghost", ck.SORTED | ck.GHOST), ("queue+ghost", ck.QUEUE | ck.GHOST)):
+                      ("sorted+ghost", ck.SORTED | ck.GHOST), ("queue+ghost", ck.QUEUE | ck.GHOST),
+                      ("hybrid", ck.HYBRID), ("hybrid+ghost", ck.HYBRID | ck.GHOST)):
         t = ck.CuckooTable(BINS, B, 2, pol, seed=1)
         fill_once(torch, ck, t, kt, vt, st, stream)  # warm
         ms, _ = fill_once(torch, ck, t, kt, vt, st, stream)
@@ -222,7 +236,8 @@ def policy_fills(torch, ck, stream, base_keys):
         out[name] = {"table": "2^24x4", "load": LOAD, "m_inserts_per_s": round(len(keys) / ms / 1e3, 2),
                      "bins_viewed_per_insert": round(s["bins_viewed_per_insert"], 4),
                      "kicks_per_insert": round(s["kicks"] / max(1, s["inserts_ok"]), 4),
-                     "chain_max": s["chain_max"], "failed": s["inserts_failed"], "aborted": s["inserts_aborted"],
+                     "chain_max": s["chain_max"], "chain": chain_summary(t.chain_histogram()),
+                     "failed": s["inserts_failed"], "aborted": s["inserts_aborted"],
                      "claim_aborts": s["aborts"], "conflict_views": s["conflict_views"]}
         t.close()
         del t
@@ -255,7 +270,8 @@ def policy_fills(torch, ck, stream, base_keys):
                "hash_family": family,
                "m_inserts_per_s": round(n / ms / 1e3, 2),
                "bins_viewed_per_insert": round(s["bins_viewed_per_insert"], 4),
-               "chain_max": s["chain_max"], "failed": s["inserts_failed"], "aborted": s["inserts_aborted"]}
+               "chain_max": s["chain_max"], "chain": chain_summary(t.chain_histogram()),
+               "failed": s["inserts_failed"], "aborted": s["inserts_aborted"]}
         if d > 2:
             ck_key = (bins, d, load)
             if ck_key not in lookup_cache:
@@ -343,6 +359,7 @@ def multi_form(torch, ck, stream):
 
 SERVE_BINS = 1 << 26
 SERVE_PREFILL = 255013683  # floor(0.95 * 2^28)
+SERVE_CAP = 1000
 
 
 def serve_form(torch, ck, stream):
@@ -361,6 +378,10 @@ def serve_form(torch, ck, stream):
     vals = inputs.values_for(keys)
     gen_s = time.perf_counter() - t0
     table = ck.CuckooTable(SERVE_BINS, B, 2, ck.QUEUE, seed=1)
+    # chain cap 1000: at 2^28 slots and loads up to 0.965 a few concurrent
+    # walks in 10^8 pass 500 kick-outs (the serial fill's longest is ~250),
+    # and a failed insert would make the results depend on the interleaving
+    table.set_param(ck.PARAM_CHAIN_CAP, SERVE_CAP)
     kt, vt = ck.as_u32_tensor(keys), ck.as_u32_tensor(vals)
     st = torch.empty(len(keys), dtype=torch.uint8, device="cuda")
 
@@ -397,7 +418,8 @@ def serve_form(torch, ck, stream):
         return out
 
     cfg = {"wave_keys": 1 << 20, "wave_slots": 4, "load_hi": 0.97}
-    out = {"table": "2^26 x 4 (2 GiB) prefilled to 0.95 (255,013,683 keys)", "requests": 4096,
+    out = {"table": "2^26 x 4 prefilled to 0.95 (255,013,683 keys), queue-kicking, chain cap %d" % SERVE_CAP,
+           "requests": 4096,
            "sizes": "log-uniform 1..2^16 keys", "arrivals": "Poisson, 20k requests/ms", "server": cfg,
            "gen_s": round(gen_s, 1)}
     for mix in [(75, 20, 5), (50, 25, 25)]:
@@ -509,7 +531,7 @@ def run_gpu(args, rank, world, local):
     df = torch.empty(N_DELETE, dtype=torch.uint8, device="cuda")
     table = ck.CuckooTable(BINS, B, 2, ck.QUEUE, seed=seed)
     n_batches = (n + BATCH - 1) // BATCH
-    launches_per_step = n_batches + 2
+    launches_per_step = n_batches + 2  # inserts, lookup, delete (the clear is a memset)
 
     def step(rec):
         # no events between the insert launches: consecutive launches overlap
@@ -568,16 +590,16 @@ def run_gpu(args, rank, world, local):
     # roofline of the dominant kernel (the insert kernel: it takes most of the step)
     hbm, peak_kind = measured_peaks()
     viewed, kicks, ins_ok = s["bins_viewed"], s["kicks"], s["inserts_ok"]
-    # per insertion: each bin viewed = one 32-B slot sector + one 32-B metadata sector;
-    # each written slot (kicks + 1) = one 32-B slot sector write + one 32-B metadata
-    # sector atomic; 8 B of key/value in and 1 B of status out
+    # per insertion: each bin viewed = one 32-B slot sector + one 32-B metadata
+    # sector; each written slot (kicks + 1) = one slot sector write + one
+    # metadata sector atomic; 8 B of key/value in and 1 B of status out
     ins_bytes = viewed * 64 + (kicks + ins_ok) * 64 + n * 9
     bytes_per_launch = ins_bytes / n_batches
     avg_launch_ms = fill_ms / K / n_batches  # launches overlap: fill time per launch
     achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
     look_bytes = N_LOOKUP * (2 * 32 + 4 + 4 + 1)
     look_gbs = look_bytes / (look_ms / K * 1e-3) / 1e9  # per GPU, per lookup launch
-    g32 = gather_roofline(torch, ck, BINS * B * 8, 32, 1 << 26, stream)
+    g32 = gather_roofline(torch, ck, BINS * B * 8, 32, 1 << 26, stream)  # over a buffer the size of the slots
     profile = batch_profile(torch, ck, table, kt, vt, st, stream)
     roofline = {"kernel": "k_insert<4,QUEUE> (one launch per 2^20-key batch)", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",

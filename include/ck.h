@@ -58,7 +58,8 @@ extern "C" {
 #define CK_SORTED 2      /* sorted search by spawn count (Sec. 5) */
 #define CK_QUEUE 3       /* queue-kicking, hit counters, hit balancing (Sec. 6) */
 #define CK_RATTLE 4      /* rattle-kicking, d-ary only (Sec. 7) */
-#define CK_GHOST 0x100   /* ghost insertions; with RANDOM/BFS/SORTED/QUEUE, two-choice only */
+#define CK_HYBRID 5      /* sorted search / BFS hybrid: depth first, then spawn count (Sec. 5, end) */
+#define CK_GHOST 0x100   /* ghost insertions; with RANDOM/BFS/SORTED/QUEUE/HYBRID, two-choice only */
 
 /* ---- runtime parameters for ck_set_param ---- */
 #define CK_PARAM_CHAIN_CAP 1     /* kick-outs (walks), tries (rattle), bins viewed (search); default 500 */
@@ -164,6 +165,15 @@ int ck_stats(ck_table *t, ck_stats_t *out);
  * 0.5%: views[i], inserts[i] for load in [i/200, (i+1)/200).  Host arrays
  * of 200 uint64 each; synchronous. */
 int ck_load_histogram(ck_table *t, uint64_t *views, uint64_t *inserts);
+
+/* Chain lengths of the successful insertions since the last reset (Fig. D
+ * of the paper plots their distribution for walks and searches):
+ * counts[i] = insertions with i kick-outs for i < 32, with 2^(i-27) ..
+ * 2^(i-26) - 1 kick-outs for 32 <= i < 39, and with >= 4096 for i = 39.
+ * A search counts the length of the path it applied; a ghost pair 0.
+ * counts: host array of 40 uint64.  Synchronous. */
+#define CK_CHAIN_BUCKETS 40
+int ck_chain_histogram(ck_table *t, uint64_t *counts);
 
 /* Zero the counters (asynchronous on the last stream used). */
 int ck_reset_stats(ck_table *t);

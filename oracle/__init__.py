@@ -23,7 +23,7 @@ _SRC = os.path.join(_HERE, "ck_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libck_oracle.so")
 
-RANDOM, BFS, SORTED, QUEUE, RATTLE = 0, 1, 2, 3, 4
+RANDOM, BFS, SORTED, QUEUE, RATTLE, HYBRID = 0, 1, 2, 3, 4, 5
 GHOST = 0x100
 ST_OK, ST_FAILED, ST_INVALID = 0, 1, 3
 
@@ -74,6 +74,8 @@ def lib():
         L.orc_export.argtypes = [ctypes.c_void_p, u64p, u8p, u8p, u8p, u8p]
         L.orc_check_invariants.restype = ctypes.c_int
         L.orc_check_invariants.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_uint64]
+        L.orc_set_spawn.restype = ctypes.c_int
+        L.orc_set_spawn.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32]
         L.orc_set_bins_override.restype = ctypes.c_int
         L.orc_set_bins_override.argtypes = [ctypes.c_void_p, u32p, u64p, ctypes.c_uint64]
         L.orc_set_rattle_tie_resident.argtypes = [ctypes.c_void_p, ctypes.c_int]
@@ -104,8 +106,8 @@ def splitmix64_at(x: int) -> int:
 class OracleTable:
     """One serial cuckoo table.
 
-    bins, slots_per_bin (B), d, policy (RANDOM/BFS/SORTED/QUEUE/RATTLE, OR
-    GHOST), rng_seed (the kick-out draws), cap (kick-out cap for walks,
+    bins, slots_per_bin (B), d, policy (RANDOM/BFS/SORTED/QUEUE/RATTLE/HYBRID,
+    OR GHOST), rng_seed (the kick-out draws), cap (kick-out cap for walks,
     try cap for rattle, bin budget for searches), seeds (hash seeds).
     """
 
@@ -129,6 +131,11 @@ class OracleTable:
             self.close()
         except Exception:
             pass
+
+    def set_spawn(self, bin, count):
+        """Fixtures: start `bin` with spawn count `count` (0..15)."""
+        if lib().orc_set_spawn(self._h, int(bin), int(count)) != 0:
+            raise ValueError("spawn count out of range")
 
     def set_bins(self, keys, bins):
         keys = np.ascontiguousarray(keys, dtype=np.uint32)

@@ -45,6 +45,7 @@
 #define ORC_SORTED 2
 #define ORC_QUEUE 3
 #define ORC_RATTLE 4
+#define ORC_HYBRID 5
 #define ORC_GHOST 0x100
 
 #define ORC_OK 0
@@ -89,13 +90,14 @@ typedef struct {
   int32_t pslot;    /* slot (in the parent's bin) of that record */
   uint32_t next;    /* next slot of this bin not yet spawned */
   uint32_t skey;    /* spawn count of the bin when its records joined the list */
+  uint32_t depth;   /* spawns between the new key and this bin's records (roots: 0) */
 } group_t;
 
 typedef struct orc_table {
   uint64_t n;          /* bins */
   uint32_t B;          /* slots per bin */
   uint32_t d;          /* hash functions */
-  uint32_t policy;     /* ORC_RANDOM .. ORC_RATTLE */
+  uint32_t policy;     /* ORC_RANDOM .. ORC_HYBRID */
   uint32_t ghost;      /* ghost insertions on (Sec. 4) */
   uint32_t cap;        /* kick-out cap (walks), try cap (rattle), bin budget (search) */
   uint32_t rattle_tie_resident; /* debug reading: resident wins rattle ties */
@@ -278,6 +280,12 @@ void orc_destroy(orc_table *t) {
 
 void orc_set_rattle_tie_resident(orc_table *t, int on) { t->rattle_tie_resident = on ? 1 : 0; }
 void orc_set_hash_family(orc_table *t, int f) { t->hash_family = f ? 1 : 0; }
+/* Fixtures: start a bin with a given spawn count (as left by earlier searches). */
+int orc_set_spawn(orc_table *t, uint64_t bin, uint32_t count) {
+  if (bin >= t->n || count > 15) return -1;
+  t->spawn[bin] = (uint8_t)count;
+  return 0;
+}
 
 /* Fixtures: give `n` keys explicit bin choices (d per key, distinct). */
 int orc_set_bins_override(orc_table *t, const uint32_t *keys, const uint64_t *bins, uint64_t n) {
@@ -596,15 +604,30 @@ static int insert_queue(orc_table *t, uint64_t krec, const uint64_t *b) {
  * (four bits, Sec. 5); these increments persist even when the search fails
  * ("since the conception of the hash table").
  *
+ * The sorted search / BFS hybrid (end of Sec. 5) orders candidates first by
+ * the depth at which they were spawn victims (the records of b0 and b1:
+ * depth 0, the records of a bin viewed by spawning a depth-k record: k + 1)
+ * and then by spawn count, oldest first on ties; it updates spawn counts as
+ * sorted search does.  Reading: the paper notes the hybrid needs no cycle
+ * monitoring; it keeps the same visited set anyway, so that all three
+ * searches count bins viewed the same way.
+ *
  * Candidates are kept as groups, one per viewed bin, in the order the bins
  * were viewed; a group's records are popped in slot order.  The budget is
  * the number of bins viewed (b0 and b1 included). */
 static int pick_group(const orc_table *t) {
   int best = -1;
   for (uint64_t g = 0; g < t->n_groups; g++) {
-    if (t->groups[g].next >= t->B) continue;
+    const group_t *q = &t->groups[g];
+    if (q->next >= t->B) continue;
     if (t->policy == ORC_BFS) return (int)g;
-    if (best < 0 || t->groups[g].skey < t->groups[best].skey) best = (int)g;
+    if (best < 0) { best = (int)g; continue; }
+    const group_t *b = &t->groups[best];
+    if (t->policy == ORC_HYBRID) {
+      if (q->depth < b->depth || (q->depth == b->depth && q->skey < b->skey)) best = (int)g;
+    } else if (q->skey < b->skey) {
+      best = (int)g;
+    }
   }
   return best;
 }
@@ -617,6 +640,7 @@ static void push_group(orc_table *t, uint64_t bin, int32_t parent, int32_t pslot
   g->pslot = pslot;
   g->next = 0;
   g->skey = t->spawn[bin];
+  g->depth = parent < 0 ? 0 : t->groups[parent].depth + 1;
   grow((void **)&t->visited_list, &t->visited_capacity, t->n_visited + 1, 8);
   t->visited[bin] = 1;
   t->visited_list[t->n_visited++] = bin;
@@ -647,7 +671,7 @@ static int insert_search(orc_table *t, uint64_t krec, const uint64_t *b) {
     uint64_t r = t->rec[gb * t->B + s];
     uint64_t y = other_bin(t, r, gb);
     if (t->visited[y]) continue;
-    if (t->policy == ORC_SORTED && t->spawn[gb] < 15) t->spawn[gb]++;
+    if ((t->policy == ORC_SORTED || t->policy == ORC_HYBRID) && t->spawn[gb] < 15) t->spawn[gb]++;
     if (t->cur_viewed == t->cap) return ORC_FAILED; /* budget spent */
     view(t);
     int f = lowest_free(t, y);
@@ -765,7 +789,7 @@ static int insert_one(orc_table *t, uint32_t key, uint32_t val, uint32_t *viewed
     st = (t->policy == ORC_RATTLE) ? insert_rattle(t, krec, b) : insert_random_dary(t, krec, b);
   } else if (t->policy == ORC_QUEUE) {
     st = insert_queue(t, krec, b);
-  } else if (t->policy == ORC_BFS || t->policy == ORC_SORTED) {
+  } else if (t->policy == ORC_BFS || t->policy == ORC_SORTED || t->policy == ORC_HYBRID) {
     st = insert_search(t, krec, b);
   } else {
     st = insert_random2(t, krec, b);

@@ -19,8 +19,9 @@ from . import build as _build
 OK, EINVAL, ENOMEM, ECUDA, EBUSY, ENOTSUP = 0, -1, -2, -3, -4, -5
 # per-key insert status
 ST_OK, ST_FAILED, ST_ABORTED, ST_INVALID = 0, 1, 2, 3
+CHAIN_BUCKETS = 40  # CK_CHAIN_BUCKETS
 # policies (Sec. 3-7) and the ghost flag (Sec. 4)
-RANDOM, BFS, SORTED, QUEUE, RATTLE = 0, 1, 2, 3, 4
+RANDOM, BFS, SORTED, QUEUE, RATTLE, HYBRID = 0, 1, 2, 3, 4, 5
 GHOST = 0x100
 # parameters
 PARAM_CHAIN_CAP, PARAM_MAX_RETRIES, PARAM_RNG_SEED = 1, 2, 3
@@ -29,7 +30,8 @@ PARAM_RATTLE_TIE_RESIDENT, PARAM_ORDERED_WRITES, PARAM_OVERLAP, PARAM_HASH_FAMIL
 INS_SERIAL = 1
 HIST_BUCKETS = 200
 
-POLICY_NAMES = {"random": RANDOM, "bfs": BFS, "sorted": SORTED, "queue": QUEUE, "rattle": RATTLE}
+POLICY_NAMES = {"random": RANDOM, "bfs": BFS, "sorted": SORTED, "queue": QUEUE, "rattle": RATTLE,
+                "hybrid": HYBRID}
 
 
 class CkStats(ctypes.Structure):
@@ -75,6 +77,7 @@ def load(build_if_missing: bool = True):
     L.ck_stats.argtypes = [_vp, ctypes.POINTER(CkStats)]
     L.ck_load_histogram.argtypes = [_vp, _vp, _vp]
     L.ck_reset_stats.argtypes = [_vp]
+    L.ck_chain_histogram.argtypes = [_vp, _vp]
     L.ck_clear.argtypes = [_vp, _vp]
     L.ck_export.argtypes = [_vp, _vp, _vp]
     L.ck_destroy.argtypes = [_vp]
@@ -127,7 +130,7 @@ class CuckooTable:
     """A cuckoo table in device memory owned by a torch tensor.
 
     bins, slots_per_bin (4 or 8 with d=2; 1 with d=3/4), d, policy
-    (RANDOM/BFS/SORTED/QUEUE, optionally | GHOST; RATTLE/RANDOM for d-ary),
+    (RANDOM/BFS/SORTED/QUEUE/HYBRID, optionally | GHOST; RATTLE/RANDOM for d-ary),
     seed: the kick-out draw seed.
     """
 
@@ -220,6 +223,13 @@ class CuckooTable:
         s = CkStats()
         _check(load().ck_stats(self._h, ctypes.byref(s)), "ck_stats")
         return {name: getattr(s, name) for name, _ in CkStats._fields_}
+
+    def chain_histogram(self) -> np.ndarray:
+        """Successful insertions by chain length (CHAIN_BUCKETS buckets, see
+        ck_chain_histogram)."""
+        out = np.zeros(CHAIN_BUCKETS, dtype=np.uint64)
+        _check(load().ck_chain_histogram(self._h, out.ctypes.data_as(_vp)), "ck_chain_histogram")
+        return out
 
     def reset_stats(self):
         _check(load().ck_reset_stats(self._h), "ck_reset_stats")

@@ -45,7 +45,7 @@ constexpr uint32_t RATTLE_SHIFT = 8;
 constexpr uint32_t HIT_ONE = 1u << HIT_SHIFT;
 constexpr uint32_t VER_ONE = 1u << VER_SHIFT;
 
-enum Policy : uint32_t { P_RANDOM = 0, P_BFS = 1, P_SORTED = 2, P_QUEUE = 3, P_RATTLE = 4 };
+enum Policy : uint32_t { P_RANDOM = 0, P_BFS = 1, P_SORTED = 2, P_QUEUE = 3, P_RATTLE = 4, P_HYBRID = 5 };
 // ST_CONFLICT: a claim lost a race, retry; ST_LONG: the local plan is full,
 // continue with a scratch-backed plan.
 enum Status : int { ST_OK = 0, ST_FAILED = 1, ST_ABORTED = 2, ST_INVALID = 3, ST_CONFLICT = 100, ST_LONG = 101 };
@@ -57,11 +57,26 @@ enum Counter : int {
   C_DELETE_HITS, C_DELETE_ABORTS, C_REVIEWS, C_VIEWED_ALL, C_N = 24
 };
 constexpr int HIST_BUCKETS = 200;
+// chain-length histogram of successful insertions: kick-outs k < 32 exact,
+// then one bucket per power of two (32-63, ..., 2048-4095), then >= 4096
+constexpr int CHAIN_BUCKETS = 40;
+// the counter block of a table: C_N counters, the bins-viewed histogram by
+// load (2 x HIST_BUCKETS), the chain-length histogram
+constexpr int COUNTER_WORDS = C_N + 2 * HIST_BUCKETS + CHAIN_BUCKETS;
+constexpr int CHAIN_HIST = C_N + 2 * HIST_BUCKETS;
+
+__host__ __device__ inline uint32_t chain_bucket(uint32_t kicks) {
+  if (kicks < 32) return kicks;
+  uint32_t lg = 31;
+  while (!((kicks >> lg) & 1u)) lg--;  // floor(log2(kicks)), 5 <= lg <= 31
+  uint32_t b = 27 + lg;
+  return b < CHAIN_BUCKETS - 1 ? b : CHAIN_BUCKETS - 1;
+}
 
 struct DevTable {
   uint64_t* slots;
   uint32_t* meta;
-  unsigned long long* counters;  // C_N counters, then 2 * HIST_BUCKETS histogram
+  unsigned long long* counters;  // COUNTER_WORDS: C_N counters, then the histograms
   uint8_t* scratch;              // search scratch, SEARCH_REGION bytes per searcher
   uint8_t* long_scratch;         // n_long plans of LONG_REGION bytes
   uint32_t* long_busy;           // n_long flags: plan region in use
@@ -270,9 +285,6 @@ __device__ __forceinline__ void load_view(const DevTable& t, uint32_t bin, View<
 // one acquire fence, then both bins' slots, so each view's slots are read
 // after its metadata word (what load_view's acquire gives) at the cost of
 // two round trips instead of three.
-#ifndef CK_VIEW2
-#define CK_VIEW2 1
-#endif
 template <int B>
 __device__ __forceinline__ void load_slots(const DevTable& t, uint32_t bin, View<B>& v) {
   const uint64_t* p = t.slots + (uint64_t)bin * B;
@@ -296,16 +308,11 @@ __device__ __forceinline__ void load_view_fast(const DevTable& t, uint32_t bin, 
 
 template <int B>
 __device__ __forceinline__ void load_view2(const DevTable& t, uint32_t b0, uint32_t b1, View<B>& v0, View<B>& v1) {
-#if CK_VIEW2
   v0.m = ld_relaxed(t.meta + b0);
   v1.m = ld_relaxed(t.meta + b1);
   fence_acquire();
   load_slots<B>(t, b0, v0);
   load_slots<B>(t, b1, v1);
-#else
-  load_view<B>(t, b0, v0);
-  load_view<B>(t, b1, v1);
-#endif
 }
 
 // Slot s of a view, s known only at run time: a chain of selects keeps the

@@ -51,10 +51,7 @@ __device__ __forceinline__ uint32_t e_new_r(uint64_t e) { return (uint32_t)(e >>
 // The first REG_ENTRIES entries of a plan stay in registers (most chains
 // are one or two slots long); the rest go to memory at pe, indexed by entry
 // number (the first REG_ENTRIES places there stay unused).
-#ifndef CK_REG_ENTRIES
-#define CK_REG_ENTRIES 2
-#endif
-constexpr int REG_ENTRIES = CK_REG_ENTRIES;
+constexpr int REG_ENTRIES = 1;  // measured: 1 is as fast as 2 and frees registers
 static_assert(REG_ENTRIES >= 0 && REG_ENTRIES <= 2, "at most two plan entries in registers");
 
 struct Ctx {
@@ -164,10 +161,6 @@ __device__ __forceinline__ bool claim(const DevTable& t, Ctx& c, uint32_t bin, u
   put_entry(c, pack_entry(bin, s, kind, hit, old_r, new_r), content);
   return true;
 }
-
-#ifndef CK_DIRECT
-#define CK_DIRECT 1
-#endif
 
 // A new key straight into free slot s of `bin` (tables without ghosts):
 // one 64-bit compare-and-swap of the slot from empty to the record, then a
@@ -346,16 +339,7 @@ __device__ int insert_random2(const DevTable& t, Ctx& c) {
   uint32_t b0, b1;
   bins2(t, c.key, b0, b1);
   View<B> v0, v1;
-  if (!CK_DIRECT && !GHOST) {
-    load_view<B>(t, b0, v0);
-    c.viewed++;
-    int s = lowest(free_mask<B>(v0));
-    if (s >= 0) return take_free<B>(t, c, b0, v0, s, false);
-    load_view<B>(t, b1, v1);
-    c.viewed++;
-    s = lowest(free_mask<B>(v1));
-    if (s >= 0) return take_free<B>(t, c, b1, v1, s, false);
-  } else if (!GHOST) {
+  if (!GHOST) {
     // the first free slot of b0, then of b1, placed by a compare-and-swap
     // of the slot on unordered views
     load_view_fast<B>(t, b0, v0);
@@ -426,17 +410,13 @@ __device__ int insert_random2(const DevTable& t, Ctx& c) {
 // The claim of a slot and the increment of the bin's hit counter are one
 // compare-and-swap, the GPU form of the paper's fetch-and-add scheduling:
 // B insertions arriving at one bin are handed B different slots.
-#ifndef CK_WALK_PREFETCH
-#define CK_WALK_PREFETCH 1
-#endif
-
 template <int B, bool GHOST>
 __device__ int insert_queue(const DevTable& t, Ctx& c) {
   constexpr uint32_t FULL = (1u << B) - 1;
   uint32_t b0, b1;
   bins2(t, c.key, b0, b1);
   View<B> v0, v1;
-  if (CK_DIRECT && !GHOST) {
+  if (!GHOST) {
     // the common case first: a free slot in the less full bin, placed by a
     // compare-and-swap of the slot on an unordered view
     load_view_fast<B>(t, b0, v0);
@@ -502,21 +482,15 @@ __device__ int insert_queue(const DevTable& t, Ctx& c) {
         if (int r0 = plan_room(t, c)) return r0;
         const uint64_t victim = slot_of<B>(vx, s);
         const uint32_t xn = other_bin2(t, victim, x);
-#if CK_WALK_PREFETCH
         // the next bin's metadata word travels with the claim; a fence
         // then orders it before that bin's slots
         const uint32_t mn = ld_relaxed(t.meta + xn);
-#endif
         if (claim(t, c, x, vx.m, s, K_MOVE, true, victim)) {
           c.kicks++;
           x = xn;
-#if CK_WALK_PREFETCH
           vx.m = mn;
           fence_acquire();
           load_slots<B>(t, x, vx);
-#else
-          load_view<B>(t, x, vx);
-#endif
           break;
         }
       }

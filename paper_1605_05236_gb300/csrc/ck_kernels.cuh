@@ -29,8 +29,8 @@ __device__ __forceinline__ int attempt_insert(const DevTable& t, Ctx& c, uint8_t
     return POL == P_RATTLE ? insert_rattle(t, c) : insert_random_dary(t, c);
   } else if constexpr (POL == P_QUEUE) {
     return insert_queue<B, GHOST>(t, c);
-  } else if constexpr (POL == P_BFS || POL == P_SORTED) {
-    return insert_search<B, POL == P_SORTED, GHOST>(t, c, region);
+  } else if constexpr (POL == P_BFS || POL == P_SORTED || POL == P_HYBRID) {
+    return insert_search<B, POL, GHOST>(t, c, region);
   } else {
     return insert_random2<B, GHOST>(t, c);
   }
@@ -113,24 +113,23 @@ __device__ __forceinline__ int insert_one(const DevTable& t, Ctx& c, uint8_t* re
 // after its predecessor.  Insertions of distinct absent keys commute under
 // the claim protocol, so the overlap changes no result.  `load_base` is the
 // number of keys the table held before this batch (for the histogram).
-#if defined(CK_INSERT_MIN_BLOCKS) && CK_INSERT_MIN_BLOCKS > 0
-#define CK_INSERT_BOUNDS __launch_bounds__(256, CK_INSERT_MIN_BLOCKS)
-#else
-#define CK_INSERT_BOUNDS __launch_bounds__(256)
-#endif
-
+// At most 64 registers (4 blocks of 256 or 8 of 128 threads per SM):
+// measured faster than the 80-96 the compiler picks unbounded, since the
+// kernel is bound by how many random accesses are in flight.
 template <int B, int POL, bool GHOST, bool SERIAL>
-__global__ void CK_INSERT_BOUNDS k_insert(DevTable t, const uint32_t* __restrict__ keys,
+__global__ void __launch_bounds__(256, 4) k_insert(DevTable t, const uint32_t* __restrict__ keys,
                                                 const uint32_t* __restrict__ vals, uint64_t n,
                                                 uint8_t* __restrict__ status,
                                                 uint32_t* __restrict__ viewed_out, uint64_t load_base) {
   asm volatile("griddepcontrol.launch_dependents;");
   __shared__ unsigned int h_views[HIST_BUCKETS];
   __shared__ unsigned int h_cnt[HIST_BUCKETS];
+  __shared__ unsigned int h_chain[CHAIN_BUCKETS];
   __shared__ unsigned long long bc[C_N];
   __shared__ unsigned long long s_next;  // next key of this block's range
   __shared__ int s_slab, s_long;
   for (int i = threadIdx.x; i < HIST_BUCKETS; i += blockDim.x) h_views[i] = h_cnt[i] = 0;
+  for (int i = threadIdx.x; i < CHAIN_BUCKETS; i += blockDim.x) h_chain[i] = 0;
   for (int i = threadIdx.x; i < C_N; i += blockDim.x) bc[i] = 0;
   // each block owns a contiguous range of the batch; its threads pull keys
   // from it one at a time, so a thread held up by a long chain does not
@@ -180,12 +179,16 @@ __global__ void CK_INSERT_BOUNDS k_insert(DevTable t, const uint32_t* __restrict
     c.krec = ((uint64_t)key << 32) | vals[i];
     c.viewed = 0;
     c.reviews = 0;
-    int st = usable ? insert_one<B, POL, GHOST>(t, c, region, aborts, local_e, local_cap, !SERIAL && POL == P_RANDOM)
+    // concurrent mode retries a failed attempt (up to three times): other
+    // insertions moved records meanwhile, so the next walk or search differs;
+    // the serial replay never retries
+    int st = usable ? insert_one<B, POL, GHOST>(t, c, region, aborts, local_e, local_cap, !SERIAL)
                     : (int)ST_ABORTED;
     if (st == ST_OK) {
       ok++;
       kicks += c.kicks;
       chain_max = max(chain_max, c.kicks);
+      atomicAdd(&h_chain[chain_bucket(c.kicks)], 1u);
       ghosts += c.ghosts_made;
       dupev += c.dup_evict;
     } else if (st == ST_FAILED) {
@@ -236,6 +239,8 @@ __global__ void CK_INSERT_BOUNDS k_insert(DevTable t, const uint32_t* __restrict
       atomicAdd(hist + HIST_BUCKETS + i, (unsigned long long)h_cnt[i]);
     }
   }
+  for (int i = threadIdx.x; i < CHAIN_BUCKETS; i += blockDim.x)
+    if (h_chain[i]) atomicAdd(t.counters + CHAIN_HIST + i, (unsigned long long)h_chain[i]);
   if (threadIdx.x == 0) {
     if (s_slab >= 0) { __threadfence(); atomicExch(t.slab_busy + s_slab, 0u); }
     if (s_long >= 0) release_long(t, s_long);
@@ -279,10 +284,6 @@ __device__ __forceinline__ void load_bin_nc(const DevTable& t, uint32_t bin, uin
 
 // Two-choice lookup: both bins are fetched at once (two independent sector
 // loads in flight per key).
-#ifndef CK_LOOKUP_EARLY
-#define CK_LOOKUP_EARLY 0
-#endif
-
 template <int B>
 __global__ void __launch_bounds__(256) k_lookup2(DevTable t, const uint32_t* __restrict__ keys, uint64_t n,
                                                  uint32_t* __restrict__ vals_out,
@@ -300,21 +301,10 @@ __global__ void __launch_bounds__(256) k_lookup2(DevTable t, const uint32_t* __r
       uint32_t b0, b1;
       bins2(t, key, b0, b1);
       uint64_t s0[B], s1[B];
-#if CK_LOOKUP_EARLY
-      // second bin only when the first does not hold the key: fewer bytes
-      // for hits in b0, a second round trip for the rest
-      load_bin_nc<B>(t, b0, s0);
-      f = match_bin<B>(s0, key, val);
-      if (!f) {
-        load_bin_nc<B>(t, b1, s1);
-        f = match_bin<B>(s1, key, val);
-      }
-#else
       load_bin_nc<B>(t, b0, s0);
       load_bin_nc<B>(t, b1, s1);
       f = match_bin<B>(s0, key, val);
       if (!f) f = match_bin<B>(s1, key, val);
-#endif
     }
     hits += f;
     cnt++;

@@ -40,7 +40,7 @@ bool shape_ok(uint64_t bins, uint32_t B, uint32_t d, uint32_t policy) {
   if (bins < 2 || bins >= (1ull << 32)) return false;
   if (d == 2) {
     if (B != 4 && B != 8) return false;
-    if (pol > CK_QUEUE) return false;
+    if (pol > CK_QUEUE && pol != CK_HYBRID) return false;
   } else if (d == 3 || d == 4) {
     if (B != 1 || ghost) return false;
     if (pol != CK_RANDOM && pol != CK_RATTLE) return false;
@@ -53,7 +53,7 @@ bool shape_ok(uint64_t bins, uint32_t B, uint32_t d, uint32_t policy) {
 
 bool is_search(uint32_t policy) {
   uint32_t pol = policy & 0xFF;
-  return pol == CK_BFS || pol == CK_SORTED;
+  return pol == CK_BFS || pol == CK_SORTED || pol == CK_HYBRID;
 }
 
 uint32_t searchers_for(uint64_t bins) {
@@ -86,7 +86,7 @@ Layout layout(uint64_t bins, uint32_t B, uint32_t policy) {
   L.meta = off;
   off = align_up(off + bins * sizeof(uint32_t));
   L.counters = off;
-  off = align_up(off + (C_N + 2 * HIST_BUCKETS) * sizeof(uint64_t));
+  off = align_up(off + COUNTER_WORDS * sizeof(uint64_t));
   L.busy = off;
   off = align_up(off + long_plans_for(bins, B, policy) * sizeof(uint32_t));
   L.slab_busy = off;
@@ -220,6 +220,7 @@ InsertFn pick_two_choice(uint32_t pol, bool ghost) {
     case CK_RANDOM: return ghost ? launch_insert<B, P_RANDOM, true> : launch_insert<B, P_RANDOM, false>;
     case CK_BFS: return ghost ? launch_insert<B, P_BFS, true> : launch_insert<B, P_BFS, false>;
     case CK_SORTED: return ghost ? launch_insert<B, P_SORTED, true> : launch_insert<B, P_SORTED, false>;
+    case CK_HYBRID: return ghost ? launch_insert<B, P_HYBRID, true> : launch_insert<B, P_HYBRID, false>;
     case CK_QUEUE: return ghost ? launch_insert<B, P_QUEUE, true> : launch_insert<B, P_QUEUE, false>;
     default: return nullptr;
   }
@@ -465,6 +466,15 @@ int ck_load_histogram(ck_table* t, uint64_t* views, uint64_t* inserts) {
   return CK_OK;
 }
 
+int ck_chain_histogram(ck_table* t, uint64_t* counts) {
+  if (!t || !counts) return CK_EINVAL;
+  if (cudaStreamSynchronize(t->last) != cudaSuccess) return CK_ECUDA;
+  if (cudaMemcpy(counts, t->dt.counters + CHAIN_HIST, CHAIN_BUCKETS * sizeof(uint64_t), cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return CK_ECUDA;
+  return CK_OK;
+}
+
 int ck_reset_stats(ck_table* t) {
   if (!t) return CK_EINVAL;
   // keep the size and the live ghost pairs: they describe the table, not the run
@@ -473,7 +483,7 @@ int ck_reset_stats(ck_table* t) {
   if (cudaMemcpy(keep, t->dt.counters + C_SIZE, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost) !=
       cudaSuccess)
     return CK_ECUDA;
-  if (cudaMemset(t->dt.counters, 0, (C_N + 2 * HIST_BUCKETS) * sizeof(uint64_t)) != cudaSuccess) return CK_ECUDA;
+  if (cudaMemset(t->dt.counters, 0, COUNTER_WORDS * sizeof(uint64_t)) != cudaSuccess) return CK_ECUDA;
   if (cudaMemcpy(t->dt.counters + C_SIZE, keep, 2 * sizeof(unsigned long long), cudaMemcpyHostToDevice) !=
       cudaSuccess)
     return CK_ECUDA;

@@ -75,7 +75,7 @@ struct MultiLayout {
 size_t table_bytes(const ck_multi_desc& d) {
   size_t b = align_up(d.bins * d.slots_per_bin * sizeof(uint64_t));
   b += align_up(d.bins * sizeof(uint32_t));
-  b += align_up((C_N + 2 * HIST_BUCKETS) * sizeof(uint64_t));
+  b += align_up(COUNTER_WORDS * sizeof(uint64_t));
   return b;
 }
 
@@ -122,7 +122,7 @@ MultiLayout multi_layout(const ck_multi_desc* d, uint32_t n) {
 
 // Persistent batched insert: blocks pull tiles, threads pull keys.
 template <int POL, bool GHOST>
-__global__ void __launch_bounds__(256) k_multi_insert(const DevTable* __restrict__ tables,
+__global__ void __launch_bounds__(256, 4) k_multi_insert(const DevTable* __restrict__ tables,
                                                       const Tile* __restrict__ tiles, uint32_t n_tiles,
                                                       unsigned long long* tile_ctr,
                                                       const uint32_t* __restrict__ keys,
@@ -163,8 +163,8 @@ __global__ void __launch_bounds__(256) k_multi_insert(const DevTable* __restrict
       c.krec = ((uint64_t)key << 32) | vals[i];
       c.viewed = 0;
       c.reviews = 0;
-      int st = t.B == 4 ? insert_one<4, POL, GHOST>(t, c, nullptr, aborts, store.e, MAX_CHAIN, POL == P_RANDOM)
-                        : insert_one<8, POL, GHOST>(t, c, nullptr, aborts, store.e, MAX_CHAIN, POL == P_RANDOM);
+      int st = t.B == 4 ? insert_one<4, POL, GHOST>(t, c, nullptr, aborts, store.e, MAX_CHAIN, true)
+                        : insert_one<8, POL, GHOST>(t, c, nullptr, aborts, store.e, MAX_CHAIN, true);
       if (st == ST_OK) {
         ok++;
         kicks += c.kicks;
@@ -307,7 +307,7 @@ int clear_tables(ck_multi* m, cudaStream_t s) {
     const DevTable& t = m->host_tables[i];
     if (cudaMemsetAsync(t.slots, 0xFF, t.total_slots * sizeof(uint64_t), s) != cudaSuccess) return CK_ECUDA;
     if (cudaMemsetAsync(t.meta, 0, t.n_bins * sizeof(uint32_t), s) != cudaSuccess) return CK_ECUDA;
-    if (cudaMemsetAsync(t.counters, 0, (C_N + 2 * HIST_BUCKETS) * sizeof(uint64_t), s) != cudaSuccess)
+    if (cudaMemsetAsync(t.counters, 0, COUNTER_WORDS * sizeof(uint64_t), s) != cudaSuccess)
       return CK_ECUDA;
   }
   m->last = s;

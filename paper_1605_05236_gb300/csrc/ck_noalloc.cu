@@ -134,6 +134,7 @@ int dispatch2(const DevTable& dt, uint8_t* sp, const uint32_t* k, const uint32_t
     case CK_RANDOM: g ? launch<B, P_RANDOM, true>(dt, sp, k, v, n, st, s) : launch<B, P_RANDOM, false>(dt, sp, k, v, n, st, s); break;
     case CK_BFS: g ? launch<B, P_BFS, true>(dt, sp, k, v, n, st, s) : launch<B, P_BFS, false>(dt, sp, k, v, n, st, s); break;
     case CK_SORTED: g ? launch<B, P_SORTED, true>(dt, sp, k, v, n, st, s) : launch<B, P_SORTED, false>(dt, sp, k, v, n, st, s); break;
+    case CK_HYBRID: g ? launch<B, P_HYBRID, true>(dt, sp, k, v, n, st, s) : launch<B, P_HYBRID, false>(dt, sp, k, v, n, st, s); break;
     case CK_QUEUE: g ? launch<B, P_QUEUE, true>(dt, sp, k, v, n, st, s) : launch<B, P_QUEUE, false>(dt, sp, k, v, n, st, s); break;
     default: return CK_ENOTSUP;
   }

@@ -1,6 +1,6 @@
-// ck_search.cuh -- breadth-first search and sorted search for a kick-out
-// chain (Kuszmaul, arXiv:1605.05236, Sec. 5), with ghost insertions (Sec. 4)
-// and claim flags (Sec. 8).
+// ck_search.cuh -- breadth-first search, sorted search and their hybrid
+// for a kick-out chain (Kuszmaul, arXiv:1605.05236, Sec. 5), with ghost
+// insertions (Sec. 4) and claim flags (Sec. 8).
 //
 // Candidates are the records of the bins viewed so far that have not been
 // spawned, kept as groups (one per viewed bin, in viewing order; a group's
@@ -12,7 +12,10 @@
 // a candidate's count is its bin's spawn count when the bin was viewed
 // (the bucket-sort key of Sec. 5).  Spawning a record increments the spawn
 // count of its bin (4 bits, saturating), and the increment stays even if
-// the search fails.
+// the search fails.  The hybrid (end of Sec. 5) orders candidates by the
+// depth at which they were spawn victims (records of b0 and b1: 0), then
+// by that spawn count, oldest first among equals, and counts spawns like
+// sorted search.
 //
 // The search itself takes no claims.  When it succeeds, every slot of the
 // path is claimed by CAS from the metadata word read when its bin was
@@ -31,9 +34,8 @@ struct Group {
   uint32_t meta;    // metadata word as viewed (updated by our own spawn increments)
   uint32_t parent;  // (group << 3) | slot of the record that led here; ~0u at a root
   uint8_t next;     // next slot to pop
-  uint8_t skey;     // sort key: spawn count when viewed
   uint8_t stale;    // the bin changed under us: a path through it aborts
-  uint8_t pad;
+  uint16_t key;     // sort key: spawn count when viewed (hybrid: depth * 16 + that count)
 };
 static_assert(sizeof(Group) == 16, "group record is 16 bytes");
 
@@ -60,12 +62,13 @@ __device__ __forceinline__ bool vis_has(const uint64_t* vis, uint32_t gen, uint3
   }
 }
 
-template <int B, bool SORTED, bool GHOST>
+// ORDER: P_BFS, P_SORTED or P_HYBRID
+template <int B, int ORDER, bool GHOST>
 __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
   uint32_t b0, b1;
   bins2(t, c.key, b0, b1);
   View<B> v0, v1;
-  if (CK_DIRECT && !GHOST) {
+  if (!GHOST) {
     // a free slot of b0, then of b1, placed by a compare-and-swap of the
     // slot on unordered views; the search needs ordered ones
     load_view_fast<B>(t, b0, v0);
@@ -113,9 +116,9 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
     g.meta = m;
     g.parent = parent;
     g.next = 0;
-    g.skey = (uint8_t)spawn_of(m);
+    uint32_t depth = (ORDER == P_HYBRID && parent != ~0u) ? (G[parent >> 3].key >> 4) + 1u : 0u;
+    g.key = (uint16_t)(depth * 16 + spawn_of(m));
     g.stale = 0;
-    g.pad = 0;
     G[ng++] = g;
     vis_insert(vis, gen, bin);
   };
@@ -127,11 +130,11 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
     while (head < ng && G[head].next >= B) head++;
     if (head == ng) return c.foreign ? ST_CONFLICT : ST_FAILED;  // nothing left to spawn
     uint32_t g = head;
-    if (SORTED) {
-      uint32_t best = G[head].skey;
+    if (ORDER != P_BFS) {
+      uint32_t best = G[head].key;
       for (uint32_t q = head + 1; q < ng; q++) {
         Group gq = G[q];
-        if (gq.next < B && gq.skey < best) { best = gq.skey; g = q; }
+        if (gq.next < B && gq.key < best) { best = gq.key; g = q; }
       }
     }
     Group gr = G[g];
@@ -145,7 +148,7 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
     if (rec == EMPTY) continue;
     uint32_t y = other_bin2(t, rec, gr.bin);
     if (vis_has(vis, gen, y)) continue;
-    if (SORTED && spawn_of(gr.meta) < 15) {
+    if (ORDER != P_BFS && spawn_of(gr.meta) < 15) {
       uint32_t nm = gr.meta + (1u << SPAWN_SHIFT);
       if (cas_acquire(t.meta + gr.bin, gr.meta, nm)) {
         G[g].meta = nm;

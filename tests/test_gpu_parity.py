@@ -21,12 +21,12 @@ pytestmark = pytest.mark.gpu
 
 EMPTY = np.uint64(0xFFFFFFFFFFFFFFFF)
 
-TWO_CHOICE = [ck.RANDOM, ck.BFS, ck.SORTED, ck.QUEUE, ck.RANDOM | ck.GHOST, ck.BFS | ck.GHOST,
-              ck.SORTED | ck.GHOST, ck.QUEUE | ck.GHOST]
+TWO_CHOICE = [ck.RANDOM, ck.BFS, ck.SORTED, ck.QUEUE, ck.HYBRID, ck.RANDOM | ck.GHOST, ck.BFS | ck.GHOST,
+              ck.SORTED | ck.GHOST, ck.QUEUE | ck.GHOST, ck.HYBRID | ck.GHOST]
 
 
 def pname(p):
-    base = {0: "random", 1: "bfs", 2: "sorted", 3: "queue", 4: "rattle"}[p & 0xFF]
+    base = {0: "random", 1: "bfs", 2: "sorted", 3: "queue", 4: "rattle", 5: "hybrid"}[p & 0xFF]
     return base + ("+ghost" if p & ck.GHOST else "") + ("+hash1" if p & 0x10000 else "")
 
 
@@ -77,7 +77,7 @@ def test_serial_replay_matches_oracle_exactly(bins, B, d, policy, load):
     cap = 500
     ref, t, family = make_pair(bins, B, d, policy, 7, cap)
     policy &= 0xFFFF
-    ost, oviewed, _ = ref.insert(keys, vals, trace=True)
+    ost, oviewed, okicks = ref.insert(keys, vals, trace=True)
     viewed = torch.zeros(len(keys), dtype=torch.int32, device="cuda")
     st = t.insert(ck.as_u32_tensor(keys), ck.as_u32_tensor(vals), viewed=viewed, serial=True)
     torch.cuda.synchronize()
@@ -94,13 +94,19 @@ def test_serial_replay_matches_oracle_exactly(bins, B, d, policy, load):
         assert np.array_equal(f["dup"], e["dup"])
         if policy & 0xFF == ck.QUEUE:
             assert np.array_equal(f["hit"], e["hit"])
-        if policy & 0xFF == ck.SORTED:
+        if policy & 0xFF in (ck.SORTED, ck.HYBRID):
             assert np.array_equal(f["spawn"], e["spawn"])
     s, os_ = t.stats(), ref.stats()
     for k in ("inserts_ok", "inserts_failed", "bins_viewed", "kicks", "chain_max", "ghost_pairs_made",
               "dup_evictions", "size", "live_ghosts"):
         assert s[k] == os_[k], k
     assert s["bins_viewed_all"] == s["bins_viewed"] and s["aborts"] == 0
+    # chain lengths of the successful insertions, bucketed as ck_chain_histogram
+    want = np.zeros(ck.CHAIN_BUCKETS, dtype=np.uint64)
+    for k in np.asarray(okicks)[ost == 0]:
+        k = int(k)
+        want[k if k < 32 else min(ck.CHAIN_BUCKETS - 1, 27 + k.bit_length() - 1)] += 1
+    assert np.array_equal(t.chain_histogram(), want)
     check_table(slots, meta, bins, B, d, family)
 
 

@@ -12,7 +12,7 @@ import oracle
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 POLICIES = {"RANDOM": oracle.RANDOM, "BFS": oracle.BFS, "SORTED": oracle.SORTED,
-            "QUEUE": oracle.QUEUE, "RATTLE": oracle.RATTLE, "GHOST": oracle.GHOST}
+            "QUEUE": oracle.QUEUE, "RATTLE": oracle.RATTLE, "HYBRID": oracle.HYBRID, "GHOST": oracle.GHOST}
 STATUS = {"OK": oracle.ST_OK, "FAILED": oracle.ST_FAILED}
 
 
@@ -38,6 +38,10 @@ def parse(path):
             r = rhs.split()
             exp = dict(x.split("=") for x in r[1:])
             steps.append(("insert", key, val, STATUS[r[0]], int(exp["viewed"]), int(exp["kicks"])))
+        elif head == "set":  # set spawn <bin> = <count>: a starting state of the fixture
+            what, rhs = rest.split("=")
+            what = what.split()
+            steps.append(("set", what, int(rhs)))
         elif head == "expect":
             what, rhs = rest.split("=")
             what = what.split()
@@ -61,6 +65,10 @@ def test_golden(path):
             s, v, k = t.insert([key], [val], trace=True)
             assert (int(s[0]), int(v[0]), int(k[0])) == (st, viewed, kicks), (path, key)
             assert t.check_invariants()[0] == 0, t.check_invariants()
+        elif step[0] == "set":
+            _, what, value = step
+            assert what[0] == "spawn", what
+            t.set_spawn(int(what[1]), value)
         else:
             _, what, rhs = step
             e = t.export()

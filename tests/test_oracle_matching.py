@@ -52,8 +52,8 @@ def run_trials(d, B, policy, n_trials, seed, complete):
     return checked_ok, checked_fail
 
 
-@pytest.mark.parametrize("policy", [oracle.BFS, oracle.SORTED, oracle.BFS | oracle.GHOST,
-                                    oracle.SORTED | oracle.GHOST])
+@pytest.mark.parametrize("policy", [oracle.BFS, oracle.SORTED, oracle.HYBRID, oracle.BFS | oracle.GHOST,
+                                    oracle.SORTED | oracle.GHOST, oracle.HYBRID | oracle.GHOST])
 @pytest.mark.parametrize("B", [2, 4])
 def test_search_is_complete(policy, B):
     ok, fail = run_trials(2, B, policy, 60, 100 + B + policy, complete=True)

@@ -34,7 +34,8 @@ def curve(policy, trials=3, lo=0.97, hi=0.975, nb=NB, b=B):
 def fig_a():
     pols = {"random": oracle.RANDOM, "bfs": oracle.BFS, "sorted": oracle.SORTED,
             "queue": oracle.QUEUE, "random+ghost": oracle.RANDOM | oracle.GHOST,
-            "bfs+ghost": oracle.BFS | oracle.GHOST, "sorted+ghost": oracle.SORTED | oracle.GHOST}
+            "bfs+ghost": oracle.BFS | oracle.GHOST, "sorted+ghost": oracle.SORTED | oracle.GHOST,
+            "hybrid": oracle.HYBRID}
     return {k: curve(p) for k, p in pols.items()}
 
 
@@ -70,6 +71,14 @@ def test_ghost_helps_bfs(fig_a):
 def test_queue_beats_random(fig_a):
     # Sec. 6: queue-kicking gives far shorter chains than random kicking at high density.
     assert fig_a["queue"][0] < fig_a["random"][0] / 2
+
+
+def test_hybrid_between_sorted_and_bfs(fig_a):
+    # Sec. 5 (end): the sorted search / BFS hybrid performs between sorted
+    # search and BFS, and its depth-first order keeps its chains as short as
+    # BFS's.
+    assert fig_a["sorted"][0] < fig_a["hybrid"][0] < fig_a["bfs"][0]
+    assert fig_a["hybrid"][1] <= fig_a["bfs"][1] * 1.05
 
 
 def test_search_chains_an_order_shorter(fig_a):

@@ -6,9 +6,9 @@ import pytest
 import oracle
 from paper_1605_05236_gb300 import inputs
 
-TWO_CHOICE = [oracle.RANDOM, oracle.BFS, oracle.SORTED, oracle.QUEUE,
+TWO_CHOICE = [oracle.RANDOM, oracle.BFS, oracle.SORTED, oracle.QUEUE, oracle.HYBRID,
               oracle.RANDOM | oracle.GHOST, oracle.BFS | oracle.GHOST,
-              oracle.SORTED | oracle.GHOST, oracle.QUEUE | oracle.GHOST]
+              oracle.SORTED | oracle.GHOST, oracle.QUEUE | oracle.GHOST, oracle.HYBRID | oracle.GHOST]
 DARY = [(3, oracle.RANDOM), (4, oracle.RANDOM), (3, oracle.RATTLE), (4, oracle.RATTLE)]
 
 
@@ -118,9 +118,10 @@ def test_queue_bins_fill_in_hit_order(ghost):
             assert occ[b].all()
 
 
-def test_spawn_counts_stay_within_four_bits():
+@pytest.mark.parametrize("policy", [oracle.SORTED, oracle.HYBRID])
+def test_spawn_counts_stay_within_four_bits(policy):
     """Sec. 5: spawn counts saturate at 15."""
-    t = oracle.OracleTable(512, 4, 2, oracle.SORTED, rng_seed=1, cap=500)
+    t = oracle.OracleTable(512, 4, 2, policy, rng_seed=1, cap=500)
     keys, _ = inputs.distinct_keys(int(512 * 4 * 0.975), 51)
     t.insert(keys, inputs.values_for(keys))
     assert t.export()["spawn"].max() <= 15
