@@ -616,10 +616,13 @@ static int insert_queue(orc_table *t, uint64_t krec, const uint64_t *b) {
  * were viewed; a group's records are popped in slot order.  The budget is
  * the number of bins viewed (b0 and b1 included). */
 static int pick_group(const orc_table *t) {
+  /* a two-choice group spawns its B records; a d-ary group (one record)
+   * tries its record's d bins */
+  const uint32_t width = t->B == 1 ? t->d : t->B;
   int best = -1;
   for (uint64_t g = 0; g < t->n_groups; g++) {
     const group_t *q = &t->groups[g];
-    if (q->next >= t->B) continue;
+    if (q->next >= width) continue;
     if (t->policy == ORC_BFS) return (int)g;
     if (best < 0) { best = (int)g; continue; }
     const group_t *b = &t->groups[best];
@@ -708,6 +711,62 @@ static int insert_search(orc_table *t, uint64_t krec, const uint64_t *b) {
 }
 
 /* ------------------------------------------------------------------ */
+/* d-ary BFS, sorted search and hybrid (Sec. 7 evaluates them; Sec. 5   */
+/* defines them)                                                       */
+/* ------------------------------------------------------------------ */
+/* Readings (Sec. 7 names the searches for d-ary tables without restating
+ * them): the first step is random kicking's, bins h_0 .. h_{d-1} viewed in
+ * order until an empty one.  If all d are full, the search starts from
+ * the key's d bins, each a group of one record.  Popping a group tries its
+ * record's next hash function (j = 0 .. d-1); the record's own bin and
+ * bins this search already viewed are skipped without a view or a spawn.
+ * Otherwise the try is a spawn: the bin holding the record gets its spawn
+ * count incremented (sorted search and hybrid; saturating at 15) and the
+ * record's j-th bin is viewed; empty ends the search with the chain
+ * root -> ... -> that bin, full makes it a new group.  Group order and the
+ * budget (bins viewed, first step included) are those of Sec. 5 above. */
+static int insert_search_dary(orc_table *t, uint64_t krec, const uint64_t *b) {
+  for (uint32_t i = 0; i < t->d; i++) {
+    view(t);
+    if (is_free(t, b[i])) { put(t, b[i], krec, 0, 0); return ORC_OK; }
+  }
+  t->n_groups = 0;
+  for (uint32_t i = 0; i < t->d; i++) push_group(t, b[i], -1, -1);
+  for (;;) {
+    int g = pick_group(t);
+    if (g < 0) return ORC_FAILED;                 /* nothing left to try */
+    uint64_t gb = t->groups[g].bin;
+    uint32_t j = t->groups[g].next++;
+    uint64_t r = t->rec[gb];
+    uint64_t rb[4];
+    bins_of(t, key_of(r), rb);
+    uint64_t y = rb[j];
+    if (y == gb || t->visited[y]) continue;
+    if ((t->policy == ORC_SORTED || t->policy == ORC_HYBRID) && t->spawn[gb] < 15) t->spawn[gb]++;
+    if (t->cur_viewed == t->cap) return ORC_FAILED; /* budget spent */
+    view(t);
+    if (is_free(t, y)) {
+      /* the chain from the root bin: the new key into the root, each
+       * displaced record into the next bin of the path, the last into y */
+      uint32_t depth = 1;
+      for (int32_t q = g; t->groups[q].parent >= 0; q = t->groups[q].parent) depth++;
+      uint64_t *path = (uint64_t *)xcalloc(depth, 8);
+      uint32_t len = 0;
+      for (int32_t q = g; q >= 0; q = t->groups[q].parent) path[len++] = t->groups[q].bin;
+      uint64_t cur = krec;
+      for (uint32_t i = len; i-- > 0;) {
+        cur = put(t, path[i], cur, 0, 0);
+        t->cur_kicks++;
+      }
+      free(path);
+      put(t, y, cur, 0, 0);
+      return ORC_OK;
+    }
+    push_group(t, y, g, (int32_t)j);
+  }
+}
+
+/* ------------------------------------------------------------------ */
 /* d-ary tables: single-slot bins, d hash functions (Sec. 7)           */
 /* ------------------------------------------------------------------ */
 /* Random kicking: bins h_0 .. h_{d-1} are viewed in order until one is
@@ -786,7 +845,9 @@ static int insert_one(orc_table *t, uint32_t key, uint32_t val, uint32_t *viewed
   begin_insert(t, key);
   int st;
   if (t->B == 1) {
-    st = (t->policy == ORC_RATTLE) ? insert_rattle(t, krec, b) : insert_random_dary(t, krec, b);
+    if (t->policy == ORC_RATTLE) st = insert_rattle(t, krec, b);
+    else if (t->policy == ORC_RANDOM) st = insert_random_dary(t, krec, b);
+    else st = insert_search_dary(t, krec, b);
   } else if (t->policy == ORC_QUEUE) {
     st = insert_queue(t, krec, b);
   } else if (t->policy == ORC_BFS || t->policy == ORC_SORTED || t->policy == ORC_HYBRID) {

@@ -26,7 +26,9 @@ __device__ __forceinline__ void backoff(uint32_t attempt, uint32_t key) {
 template <int B, int POL, bool GHOST>
 __device__ __forceinline__ int attempt_insert(const DevTable& t, Ctx& c, uint8_t* region) {
   if constexpr (B == 1) {
-    return POL == P_RATTLE ? insert_rattle(t, c) : insert_random_dary(t, c);
+    if constexpr (POL == P_RATTLE) return insert_rattle(t, c);
+    else if constexpr (POL == P_RANDOM) return insert_random_dary(t, c);
+    else return insert_search_dary<POL>(t, c, region);
   } else if constexpr (POL == P_QUEUE) {
     return insert_queue<B, GHOST>(t, c);
   } else if constexpr (POL == P_BFS || POL == P_SORTED || POL == P_HYBRID) {
@@ -90,12 +92,14 @@ __device__ __forceinline__ int insert_one(const DevTable& t, Ctx& c, uint8_t* re
       continue;
     }
     if (st == ST_FAILED) {
-      if (!retry_failed || ++fails > 3) break;
+      if (!retry_failed || ++fails > 6) break;
     } else {
       aborts++;
     }
     if (++attempt >= t.max_retries) { st = ST_ABORTED; break; }
-    if (st == ST_CONFLICT) backoff(attempt, c.key);
+    // a failed attempt waits longer before its retry: the walks and claims
+    // of the insertions around it, which made it fail, finish meanwhile
+    backoff(st == ST_FAILED ? 6 + 2 * fails : attempt, c.key);
   }
   if (c.long_id >= 0) release_long(t, c.long_id);
   return st;

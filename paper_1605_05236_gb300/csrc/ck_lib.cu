@@ -43,7 +43,7 @@ bool shape_ok(uint64_t bins, uint32_t B, uint32_t d, uint32_t policy) {
     if (pol > CK_QUEUE && pol != CK_HYBRID) return false;
   } else if (d == 3 || d == 4) {
     if (B != 1 || ghost) return false;
-    if (pol != CK_RANDOM && pol != CK_RATTLE) return false;
+    if (pol == CK_QUEUE || pol > CK_HYBRID) return false;  // d-ary: random/rattle kicking, the searches
   } else {
     return false;
   }
@@ -228,7 +228,15 @@ InsertFn pick_two_choice(uint32_t pol, bool ghost) {
 
 InsertFn pick_insert(const ck_table* t) {
   const DevTable& d = t->dt;
-  if (d.B == 1) return d.policy == CK_RATTLE ? launch_insert<1, P_RATTLE, false> : launch_insert<1, P_RANDOM, false>;
+  if (d.B == 1) {
+    switch (d.policy) {
+      case CK_RATTLE: return launch_insert<1, P_RATTLE, false>;
+      case CK_BFS: return launch_insert<1, P_BFS, false>;
+      case CK_SORTED: return launch_insert<1, P_SORTED, false>;
+      case CK_HYBRID: return launch_insert<1, P_HYBRID, false>;
+      default: return launch_insert<1, P_RANDOM, false>;
+    }
+  }
   if (d.B == 4) return pick_two_choice<4>(d.policy, d.ghost != 0);
   if (d.B == 8) return pick_two_choice<8>(d.policy, d.ghost != 0);
   return nullptr;

@@ -158,6 +158,9 @@ extern "C" int ck_insert_batch_noalloc(ck_table* t, const uint32_t* d_keys, cons
   if (dt.B == 4) rc = dispatch2<4>(dt, scratch, d_keys, d_vals, n, d_status, s);
   else if (dt.B == 8) rc = dispatch2<8>(dt, scratch, d_keys, d_vals, n, d_status, s);
   else if (dt.policy == CK_RATTLE) launch<1, P_RATTLE, false>(dt, scratch, d_keys, d_vals, n, d_status, s);
+  else if (dt.policy == CK_BFS) launch<1, P_BFS, false>(dt, scratch, d_keys, d_vals, n, d_status, s);
+  else if (dt.policy == CK_SORTED) launch<1, P_SORTED, false>(dt, scratch, d_keys, d_vals, n, d_status, s);
+  else if (dt.policy == CK_HYBRID) launch<1, P_HYBRID, false>(dt, scratch, d_keys, d_vals, n, d_status, s);
   else launch<1, P_RANDOM, false>(dt, scratch, d_keys, d_vals, n, d_status, s);
   if (rc != CK_OK) return rc;
   return cudaGetLastError() == cudaSuccess ? CK_OK : CK_ECUDA;

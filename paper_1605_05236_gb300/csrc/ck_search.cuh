@@ -209,4 +209,124 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
   }
 }
 
+// ------------------------------------------------------------------
+// d-ary tables (Sec. 7 evaluates BFS and sorted search on them): one record
+// per bin.  The first step is random kicking's (h_0, h_1, .. viewed until
+// an empty bin).  Then the key's d bins are the root groups; popping a
+// group tries its record's next hash function j (the record's own bin and
+// bins already viewed are skipped without a view or a spawn); a try is a
+// spawn (the group's bin gets its spawn count incremented for sorted
+// search and the hybrid) and views the record's j-th bin: empty ends the
+// search, full makes it a group.  Same group order, budget and claiming of
+// the path as the two-choice searches above.
+// ------------------------------------------------------------------
+template <int ORDER>
+__device__ int insert_search_dary(const DevTable& t, Ctx& c, uint8_t* region) {
+  const uint32_t d = t.d;
+  uint32_t b[4];
+  bins_of(t, c.key, b);
+  View<1> v[4];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+    if (i < (int)d) load_view<1>(t, b[i], v[i]);  // the d loads overlap
+  for (uint32_t i = 0; i < d; i++) {
+    c.viewed++;
+    if (free_mask<1>(v[i])) return take_free<1>(t, c, b[i], v[i], 0, false);
+  }
+
+  uint32_t* hdr = reinterpret_cast<uint32_t*>(region);
+  Group* G = reinterpret_cast<Group*>(region + 16);
+  uint64_t* vis = reinterpret_cast<uint64_t*>(region + 16 + MAX_GROUPS * sizeof(Group));
+  uint32_t gen = hdr[0] + 1;
+  if (gen == 0) gen = 1;
+  hdr[0] = gen;
+
+  uint32_t ng = 0, head = 0;
+  auto push = [&](uint32_t bin, uint32_t m, uint32_t parent) {
+    Group g;
+    g.bin = bin;
+    g.meta = m;
+    g.parent = parent;
+    g.next = 0;
+    uint32_t depth = (ORDER == P_HYBRID && parent != ~0u) ? (G[parent >> 3].key >> 4) + 1u : 0u;
+    g.key = (uint16_t)(depth * 16 + spawn_of(m));
+    g.stale = 0;
+    G[ng++] = g;
+    vis_insert(vis, gen, bin);
+  };
+  for (uint32_t i = 0; i < d; i++) push(b[i], v[i].m, ~0u);
+
+  for (;;) {
+    while (head < ng && G[head].next >= d) head++;
+    if (head == ng) return c.foreign ? ST_CONFLICT : ST_FAILED;  // nothing left to try
+    uint32_t g = head;
+    if (ORDER != P_BFS) {
+      uint32_t best = G[head].key;
+      for (uint32_t q = head + 1; q < ng; q++) {
+        Group gq = G[q];
+        if (gq.next < d && gq.key < best) { best = gq.key; g = q; }
+      }
+    }
+    Group gr = G[g];
+    uint32_t j = gr.next;
+    G[g].next = (uint8_t)(j + 1);
+    if (gr.meta & 1u) {  // claimed by another insertion: ignore it (Sec. 8)
+      c.foreign = 1;
+      continue;
+    }
+    uint64_t rec = ld_slot(t.slots + gr.bin);
+    if (rec == EMPTY) continue;
+    uint32_t rb[4];
+    bins_of(t, key_of(rec), rb);
+    uint32_t y = rb[j];
+    if (y == gr.bin || vis_has(vis, gen, y)) continue;
+    if (ORDER != P_BFS && spawn_of(gr.meta) < 15) {
+      uint32_t nm = gr.meta + (1u << SPAWN_SHIFT);
+      if (cas_acquire(t.meta + gr.bin, gr.meta, nm)) {
+        G[g].meta = nm;
+      } else {
+        G[g].stale = 1;
+        uint32_t m = ld_acquire(t.meta + gr.bin);
+        for (int k = 0; k < 64 && spawn_of(m) < 15; k++) {  // bounded: a lost count is harmless
+          if (cas_acquire(t.meta + gr.bin, m, m + (1u << SPAWN_SHIFT))) break;
+          m = ld_acquire(t.meta + gr.bin);
+        }
+      }
+    }
+    if (c.viewed - c.viewed0 >= t.cap || ng >= MAX_GROUPS)  // budget spent
+      return c.foreign ? ST_CONFLICT : ST_FAILED;
+    View<1> vy;
+    load_view<1>(t, y, vy);
+    c.viewed++;
+    if (claimed_mask<1>(vy)) c.foreign = 1;
+    if (!free_mask<1>(vy)) {
+      push(y, vy.m, g << 3);
+      continue;
+    }
+    // path: root group -> ... -> group g, one record each, in chain order
+    uint32_t depth = 1;
+    for (uint32_t q = g; G[q].parent != ~0u; q = G[q].parent >> 3) depth++;
+    if ((int)depth + 4 > c.pcap) return ST_LONG;
+    {
+      uint32_t q = g;
+      for (int i = (int)depth - 1; i >= 0; i--) {
+        set_entry(c, i, pack_entry(G[q].bin, 0, K_MOVE, false, 0, 0), q);
+        if (G[q].parent != ~0u) q = G[q].parent >> 3;
+      }
+    }
+    // claim the path in chain order from the metadata words as viewed; the
+    // record read after a claim is the one the search saw
+    c.pn = 0;
+    for (uint32_t i = 0; i < depth; i++) {
+      Group gq = G[(uint32_t)content_at(c, (int)i)];
+      if (gq.stale) return ST_CONFLICT;
+      if (!cas_acquire(t.meta + gq.bin, gq.meta, gq.meta + 1u)) return ST_CONFLICT;
+      c.pn = (int)i + 1;
+      set_content(c, (int)i, ld_slot(t.slots + gq.bin));
+    }
+    c.kicks = depth;
+    return take_free<1>(t, c, y, vy, 0, false);
+  }
+}
+
 }  // namespace ck

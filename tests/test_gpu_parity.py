@@ -51,7 +51,7 @@ def fill_case(bins, B, d, load, seed):
 def meta_fields(meta, B, d):
     meta = meta.astype(np.uint32)
     if d > 2:
-        return {"rattle": ((meta >> 8) & 0xFF).astype(np.uint8)}
+        return {"rattle": ((meta >> 8) & 0xFF).astype(np.uint8), "spawn": ((meta >> 16) & 0xF).astype(np.uint8)}
     dup = np.zeros(len(meta) * B, dtype=np.uint8)
     for s in range(B):
         dup[s::B] = (meta >> (8 + s)) & 1
@@ -64,7 +64,8 @@ SERIAL_CASES = (
     + [(1 << 12, 8, 2, p, 0.97) for p in TWO_CHOICE]          # 8-slot bins to 0.97
     + [(1 << 14, 1, 3, ck.RANDOM, 0.90), (1 << 14, 1, 3, ck.RATTLE, 0.90),
        (1 << 14, 1, 4, ck.RANDOM, 0.96), (1 << 14, 1, 4, ck.RATTLE, 0.96),
-       (1 << 14, 1, 3, ck.RATTLE | 0x10000, 0.90), (1 << 12, 4, 2, ck.QUEUE | 0x10000, 0.95)]
+       (1 << 14, 1, 3, ck.RATTLE | 0x10000, 0.90), (1 << 12, 4, 2, ck.QUEUE | 0x10000, 0.95),
+       (1 << 14, 1, 3, ck.BFS, 0.88), (1 << 14, 1, 4, ck.SORTED, 0.95), (1 << 14, 1, 4, ck.HYBRID, 0.95)]
 )
 # 0x10000 in a case's policy selects the decorrelated hash family (test-only marker)
 FAMILY_FLAG = 0x10000
@@ -90,6 +91,8 @@ def test_serial_replay_matches_oracle_exactly(bins, B, d, policy, load):
     if d > 2:
         if policy == ck.RATTLE:
             assert np.array_equal(f["rattle"], e["rattle"])
+        if policy in (ck.SORTED, ck.HYBRID):
+            assert np.array_equal(f["spawn"], e["spawn"])
     else:
         assert np.array_equal(f["dup"], e["dup"])
         if policy & 0xFF == ck.QUEUE:
@@ -114,7 +117,8 @@ CONCURRENT_CASES = (
     [(1 << 16, 4, 2, p, 0.95) for p in TWO_CHOICE]
     + [(1 << 15, 8, 2, p, 0.97) for p in (ck.RANDOM, ck.QUEUE, ck.SORTED | ck.GHOST)]
     + [(1 << 18, 1, 3, ck.RANDOM, 0.90), (1 << 16, 1, 4, ck.RATTLE, 0.96), (1 << 16, 1, 4, ck.RANDOM, 0.96),
-       (1 << 18, 1, 3, ck.RATTLE | 0x10000, 0.90)]
+       (1 << 18, 1, 3, ck.RATTLE | 0x10000, 0.90), (1 << 16, 1, 3, ck.BFS, 0.85),
+       (1 << 16, 1, 4, ck.SORTED, 0.93), (1 << 16, 1, 4, ck.HYBRID, 0.93)]
 )
 
 

@@ -68,6 +68,15 @@ def test_walks_never_overfill(policy, B):
     assert ok > 0 and fail > 0
 
 
+@pytest.mark.parametrize("d,policy", [(3, oracle.BFS), (4, oracle.BFS), (3, oracle.SORTED), (4, oracle.SORTED),
+                                      (3, oracle.HYBRID), (4, oracle.HYBRID)])
+def test_dary_search_is_complete(d, policy):
+    # single-slot bins: an unbounded search explores every bin reachable by
+    # an alternating path, so it fails exactly when no matching exists
+    ok, fail = run_trials(d, 1, policy, 60, 400 + d + policy, complete=True)
+    assert ok > 0 and fail > 0
+
+
 @pytest.mark.parametrize("d,policy", [(3, oracle.RANDOM), (4, oracle.RANDOM), (3, oracle.RATTLE),
                                       (4, oracle.RATTLE), (2, oracle.RANDOM)])
 def test_dary_walks_never_overfill(d, policy):

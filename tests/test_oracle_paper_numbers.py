@@ -155,6 +155,20 @@ def test_rattle_beats_random_four_ary():
     assert r / q > 2.0
 
 
+def test_sorted_search_beats_random_four_ary():
+    # Sec. 1 / Sec. 7: for 4-ary tables at high density sorted search (like
+    # rattle-kicking) views about 3x fewer bins than random kicking, and BFS
+    # is no better than random kicking.
+    n = inputs.load_target(NB, 0.95)
+    load = np.arange(n) / NB
+    m = load >= 0.93
+    r = np.mean([v[m].mean() for _, v in dary_fill(oracle.RANDOM, trials=2)])
+    s = np.mean([v[m].mean() for _, v in dary_fill(oracle.SORTED, trials=2)])
+    b = np.mean([v[m].mean() for _, v in dary_fill(oracle.BFS, trials=2)])
+    assert r / s > 2.0
+    assert b > s
+
+
 def test_curves_scale_with_table_size():
     # Sec. 3: the curves do not depend on the table size.
     small = curve(oracle.QUEUE, trials=4, lo=0.93, hi=0.95, nb=1 << 11)[0]

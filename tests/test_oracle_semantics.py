@@ -9,7 +9,8 @@ from paper_1605_05236_gb300 import inputs
 TWO_CHOICE = [oracle.RANDOM, oracle.BFS, oracle.SORTED, oracle.QUEUE, oracle.HYBRID,
               oracle.RANDOM | oracle.GHOST, oracle.BFS | oracle.GHOST,
               oracle.SORTED | oracle.GHOST, oracle.QUEUE | oracle.GHOST, oracle.HYBRID | oracle.GHOST]
-DARY = [(3, oracle.RANDOM), (4, oracle.RANDOM), (3, oracle.RATTLE), (4, oracle.RATTLE)]
+DARY = [(3, oracle.RANDOM), (4, oracle.RANDOM), (3, oracle.RATTLE), (4, oracle.RATTLE),
+        (3, oracle.BFS), (4, oracle.SORTED), (4, oracle.HYBRID)]
 
 
 def configs():
