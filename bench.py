@@ -228,8 +228,13 @@ def policy_fills(torch, ck, stream, base_keys):
     for name, pol in (("random", ck.RANDOM), ("bfs", ck.BFS), ("sorted", ck.SORTED), ("queue", ck.QUEUE),
                       ("random+ghost", ck.RANDOM | ck.GHOST), ("bfs+ghost", ck.BFS | ck.GHOST),
                       ("sorted+ghost", ck.SORTED | ck.GHOST), ("queue+ghost", ck.QUEUE | ck.GHOST),
-                      ("hybrid", ck.HYBRID), ("hybrid+ghost", ck.HYBRID | ck.GHOST)):
-        t = ck.CuckooTable(BINS, B, 2, pol, seed=1)
+                      ("hybrid", ck.HYBRID), ("hybrid+ghost", ck.HYBRID | ck.GHOST),
+                      ("bfs_k4", ck.BFS | 0x10000), ("sorted_k4", ck.SORTED | 0x10000),
+                      ("sorted+ghost_k4", ck.SORTED | ck.GHOST | 0x10000)):
+        # 0x10000 here: searches spawning 4 records a round (Sec. 5 prefetching)
+        t = ck.CuckooTable(BINS, B, 2, pol & 0xFFFF, seed=1)
+        if pol & 0x10000:
+            t.set_param(ck.PARAM_SPAWN_K, 4)
         fill_once(torch, ck, t, kt, vt, st, stream)  # warm
         ms, _ = fill_once(torch, ck, t, kt, vt, st, stream)
         s = t.stats()
@@ -255,7 +260,9 @@ def policy_fills(torch, ck, stream, base_keys):
             ("random_d4_0.96", 1 << 26, 1, 4, ck.RANDOM, 0.96, 4096),
             ("rattle_d4_0.96", 1 << 26, 1, 4, ck.RATTLE, 0.96, 500),
             ("random_d4_0.96_hash1", 1 << 26, 1, 4, ck.RANDOM | 0x10000, 0.96, 4096),
-            ("rattle_d4_0.96_hash1", 1 << 26, 1, 4, ck.RATTLE | 0x10000, 0.96, 500)):
+            ("rattle_d4_0.96_hash1", 1 << 26, 1, 4, ck.RATTLE | 0x10000, 0.96, 500),
+            ("sorted_d4_0.96", 1 << 26, 1, 4, ck.SORTED, 0.96, 500),
+            ("hybrid_d4_0.96", 1 << 26, 1, 4, ck.HYBRID, 0.96, 500)):
         n = inputs.load_target(bins * b, load)
         keys, nxt = inputs.distinct_keys(n, 2)
         kt, vt = ck.as_u32_tensor(keys), ck.as_u32_tensor(inputs.values_for(keys))
@@ -459,7 +466,16 @@ def serve_form(torch, ck, stream):
         rec["capacity_k_req_per_s"] = {"sequential": round(cap_seq / 1e3, 1), "server": round(cap_srv / 1e3, 1)}
         bad = {name: check(tr, r) for name, r in zip(run_names, runs)}
         rec["results_exact"] = all(b is None for b in bad.values())
-        if not rec["results_exact"]:
+        # the stated tolerance: an insert may come back CK_ST_FAILED (key
+        # absent, table unchanged) when its queue walk runs into its own
+        # claims in the layout this run's concurrency produced; every
+        # lookup, delete and value must still match
+        only_failed_inserts = all(
+            b is None or (b["value_mismatch"] == 0 and set(b) <= {"value_mismatch", "insert"}
+                          and set(b["insert"]["statuses"]) == {1}) for b in bad.values())
+        rec["equal_within_tolerance"] = only_failed_inserts
+        rec["failed_inserts"] = {k: (0 if b is None else b.get("insert", {}).get("wrong", 0)) for k, b in bad.items()}
+        if not only_failed_inserts:
             rec["mismatches"] = {k: b for k, b in bad.items() if b is not None}
         rec["throughput_speedup"] = round(rec["sequential_trace_rate"]["span_ms"] /
                                           rec["server_trace_rate"]["span_ms"], 3)
@@ -649,7 +665,10 @@ def run_gpu(args, rank, world, local):
 def end_to_end(torch, ck, table, keys, vals, lk, dk, stream, K):
     """The same step through the public API from pinned host buffers: each
     batch's keys/values are copied in, the statuses, lookup results and
-    delete results copied out, all inside the timed region."""
+    delete results copied out, all inside the timed region.  Copies run on
+    a second stream: batch i + 1 (and the lookup and delete keys) come in
+    while batch i is inserted, and results go out as soon as they exist --
+    the way a caller of the C ABI overlaps transfers with the launches."""
     n = len(keys)
     hk = torch.from_numpy(keys.view(np.int32)).pin_memory()
     hv = torch.from_numpy(vals.view(np.int32)).pin_memory()
@@ -659,31 +678,53 @@ def end_to_end(torch, ck, table, keys, vals, lk, dk, stream, K):
     hlv = torch.empty(len(lk), dtype=torch.int32).pin_memory()
     hlf = torch.empty(len(lk), dtype=torch.uint8).pin_memory()
     hdf = torch.empty(len(dk), dtype=torch.uint8).pin_memory()
-    dk_ = torch.empty(BATCH, dtype=torch.int32, device="cuda")
-    dv_ = torch.empty(BATCH, dtype=torch.int32, device="cuda")
-    ds_ = torch.empty(BATCH, dtype=torch.uint8, device="cuda")
+    dkey = torch.empty(n, dtype=torch.int32, device="cuda")
+    dval = torch.empty(n, dtype=torch.int32, device="cuda")
+    dst = torch.empty(n, dtype=torch.uint8, device="cuda")
     dl = torch.empty(len(lk), dtype=torch.int32, device="cuda")
     dlv = torch.empty(len(lk), dtype=torch.int32, device="cuda")
     dlf = torch.empty(len(lk), dtype=torch.uint8, device="cuda")
     ddk = torch.empty(len(dk), dtype=torch.int32, device="cuda")
     ddf = torch.empty(len(dk), dtype=torch.uint8, device="cuda")
+    cs = torch.cuda.Stream()  # copies
+    bounds = [(lo, min(n, lo + BATCH)) for lo in range(0, n, BATCH)]
 
     def step():
+        cs.wait_stream(stream)
         table.clear(stream)
-        for lo in range(0, n, BATCH):
-            hi = min(n, lo + BATCH)
-            m = hi - lo
-            dk_[:m].copy_(hk[lo:hi], non_blocking=True)
-            dv_[:m].copy_(hv[lo:hi], non_blocking=True)
-            table.insert_batch(dk_[:m], dv_[:m], ds_[:m], stream)
-            hst[lo:hi].copy_(ds_[:m], non_blocking=True)
-        dl.copy_(hl, non_blocking=True)
+        copied = []
+        with torch.cuda.stream(cs):
+            for lo, hi in bounds:  # every batch in order, each with its own event
+                dkey[lo:hi].copy_(hk[lo:hi], non_blocking=True)
+                dval[lo:hi].copy_(hv[lo:hi], non_blocking=True)
+                e = torch.cuda.Event()
+                e.record(cs)
+                copied.append(e)
+            dl.copy_(hl, non_blocking=True)
+            ddk.copy_(hd, non_blocking=True)
+            keys_in = torch.cuda.Event()
+            keys_in.record(cs)
+        for (lo, hi), e in zip(bounds, copied):
+            stream.wait_event(e)
+            table.insert_batch(dkey[lo:hi], dval[lo:hi], dst[lo:hi], stream)
+        ins_done = torch.cuda.Event()
+        ins_done.record(stream)
+        stream.wait_event(keys_in)
         table.lookup(dl, dlv, dlf, stream)
-        hlv.copy_(dlv, non_blocking=True)
-        hlf.copy_(dlf, non_blocking=True)
-        ddk.copy_(hd, non_blocking=True)
+        lk_done = torch.cuda.Event()
+        lk_done.record(stream)
         table.delete(ddk, ddf, stream)
-        hdf.copy_(ddf, non_blocking=True)
+        del_done = torch.cuda.Event()
+        del_done.record(stream)
+        with torch.cuda.stream(cs):
+            cs.wait_event(ins_done)
+            hst.copy_(dst, non_blocking=True)
+            cs.wait_event(lk_done)
+            hlv.copy_(dlv, non_blocking=True)
+            hlf.copy_(dlf, non_blocking=True)
+            cs.wait_event(del_done)
+            hdf.copy_(ddf, non_blocking=True)
+        stream.wait_stream(cs)
 
     step()
     torch.cuda.synchronize()
@@ -699,7 +740,7 @@ def end_to_end(torch, ck, table, keys, vals, lk, dk, stream, K):
     d2h = n * 1 + len(lk) * 5 + len(dk) * 1
     return {"value": round(n / (ms * 1e-3) / 1e6, 2), "unit": "M inserts/s (whole step incl. copies)",
             "ms_per_step": round(ms, 3), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "results_exact": ok}
+            "copies": "on a second stream, overlapped with the launches", "results_exact": ok}
 
 
 # ---------------------------------------------------------------------------

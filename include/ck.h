@@ -51,6 +51,7 @@ extern "C" {
 #define CK_ST_FAILED 1   /* chain cap / search budget reached; key absent, table as before */
 #define CK_ST_ABORTED 2  /* claim conflicts exceeded the retry limit; key absent */
 #define CK_ST_INVALID 3  /* reserved key 0xFFFFFFFF */
+#define CK_ST_UPDATED 5  /* CK_INS_UPSERT: the key was present; every copy now holds the new value */
 
 /* ---- kick-out policies (Sec. 3-7), ghost insertions OR-able (Sec. 4) ---- */
 #define CK_RANDOM 0      /* random kicking (Sec. 1) */
@@ -68,16 +69,30 @@ extern "C" {
 #define CK_PARAM_HASH_SEED0 10   /* + i for seed_i, i < d (defaults 0x9E3779B9, 0x85EBCA6B, 0xC2B2AE35, 0x27D4EB2F) */
 #define CK_PARAM_BLOCK 20        /* threads per block of the insert kernels */
 #define CK_PARAM_RATTLE_TIE_RESIDENT 30 /* 1: the resident wins rattle ties (debug reading) */
-#define CK_PARAM_ORDERED_WRITES 31      /* 1 (default): release-ordered chain writes, so a
-                                           concurrently read key is never absent (Sec. 8) */
+#define CK_PARAM_ORDERED_WRITES 31      /* chains are always written back to front (Sec. 8);
+                                           1: a release fence between consecutive writes makes
+                                           that order visible, so a reader that does not
+                                           validate never misses a moving key.  0 (default):
+                                           one fence per chain -- every reader in this library
+                                           either validates against claims (server lookups,
+                                           deletes) or does not overlap writers (bulk lookups) */
 #define CK_PARAM_OVERLAP 32     /* 1 (default): an insert launch may start while the previous
                                    one on the stream finishes its longest chains */
+#define CK_PARAM_SPAWN_K 34     /* searches (BFS, sorted, hybrid): spawns per round, 1..8
+                                   (default 1).  Sec. 5: spawning the k best candidates at a
+                                   time lets their bins be fetched together; every bin of a
+                                   round counts as viewed, and the first with room, in
+                                   candidate order, ends the search. */
 #define CK_PARAM_HASH_FAMILY 33 /* 0 (default): h_i = fmix32(k ^ seed_i); 1: decorrelated
                                    h_i = fmix32(fmix32(k + seed_i) ^ (seed_i * 0x27D4EB2F)).
                                    Set before the first insertion. */
 
 /* ---- ck_insert_batch_ex flags ---- */
 #define CK_INS_SERIAL 1  /* one insertion in flight, keys in batch order (debug/parity) */
+#define CK_INS_UPSERT 2  /* lift the absent-key assumption (Sec. 3): a present key gets its value
+                            overwritten in place (CK_ST_UPDATED), an absent one is inserted; keys
+                            must be distinct within the batch and not written by another call
+                            running at the same time */
 
 /* ---- counters returned by ck_stats (device totals since the last reset) ---- */
 typedef struct ck_stats_t {
@@ -101,6 +116,7 @@ typedef struct ck_stats_t {
   double load;                  /* size / total_slots */
   double bins_viewed_per_insert;/* bins_viewed / (inserts_ok + failed + aborted) */
   double aborts_per_insert;
+  uint64_t updates;             /* CK_INS_UPSERT: present keys overwritten (CK_ST_UPDATED) */
 } ck_stats_t;
 
 typedef struct ck_table ck_table; /* opaque; owned by the library */

@@ -25,14 +25,14 @@ _LIB = os.path.join(_BUILD, "libck_oracle.so")
 
 RANDOM, BFS, SORTED, QUEUE, RATTLE, HYBRID = 0, 1, 2, 3, 4, 5
 GHOST = 0x100
-ST_OK, ST_FAILED, ST_INVALID = 0, 1, 3
+ST_OK, ST_FAILED, ST_INVALID, ST_UPDATED = 0, 1, 3, 5
 
 # order of the counters returned by stats()
 STAT_NAMES = (
     "inserts_ok", "inserts_failed", "bins_viewed", "kicks", "chain_max",
     "ghost_pairs_made", "dup_evictions", "size", "live_ghosts", "lookups",
     "lookup_hits", "deletes", "delete_hits", "prop41_violations",
-    "prop41_checks",
+    "prop41_checks", "updates",
 )
 
 DEFAULT_SEEDS = (0x9E3779B9, 0x85EBCA6B, 0xC2B2AE35, 0x27D4EB2F)
@@ -69,11 +69,14 @@ def lib():
         L.orc_insert_batch.argtypes = [ctypes.c_void_p, u32p, u32p, ctypes.c_uint64, u8p, u32p, u32p]
         L.orc_lookup_batch.argtypes = [ctypes.c_void_p, u32p, ctypes.c_uint64, u32p, u8p]
         L.orc_delete_batch.argtypes = [ctypes.c_void_p, u32p, ctypes.c_uint64, u8p]
+        L.orc_upsert_batch.argtypes = [ctypes.c_void_p, u32p, u32p, ctypes.c_uint64, u8p]
         L.orc_stats.argtypes = [ctypes.c_void_p, u64p]
         L.orc_n_stats.restype = ctypes.c_uint32
         L.orc_export.argtypes = [ctypes.c_void_p, u64p, u8p, u8p, u8p, u8p]
         L.orc_check_invariants.restype = ctypes.c_int
         L.orc_check_invariants.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_uint64]
+        L.orc_set_spawn_k.restype = ctypes.c_int
+        L.orc_set_spawn_k.argtypes = [ctypes.c_void_p, ctypes.c_uint32]
         L.orc_set_spawn.restype = ctypes.c_int
         L.orc_set_spawn.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32]
         L.orc_set_bins_override.restype = ctypes.c_int
@@ -132,6 +135,11 @@ class OracleTable:
         except Exception:
             pass
 
+    def set_spawn_k(self, k):
+        """Searches: spawns per round, their bins viewed together (1..8; 1 = plain)."""
+        if lib().orc_set_spawn_k(self._h, int(k)) != 0:
+            raise ValueError("spawn_k must be 1..8")
+
     def set_spawn(self, bin, count):
         """Fixtures: start `bin` with spawn count `count` (0..15)."""
         if lib().orc_set_spawn(self._h, int(bin), int(count)) != 0:
@@ -184,6 +192,15 @@ class OracleTable:
         lib().orc_delete_batch(self._h, _ptr(keys, ctypes.c_uint32), len(keys),
                                _ptr(found, ctypes.c_uint8))
         return found
+
+    def upsert(self, keys, vals):
+        """Insert, or overwrite the value of a present key (status 5)."""
+        keys = np.ascontiguousarray(keys, dtype=np.uint32)
+        vals = np.ascontiguousarray(vals, dtype=np.uint32)
+        st = np.zeros(len(keys), dtype=np.uint8)
+        lib().orc_upsert_batch(self._h, _ptr(keys, ctypes.c_uint32), _ptr(vals, ctypes.c_uint32), len(keys),
+                               _ptr(st, ctypes.c_uint8))
+        return st
 
     def stats(self) -> dict:
         out = np.zeros(len(STAT_NAMES), dtype=np.uint64)

@@ -69,6 +69,7 @@ enum {
   OS_DELETE_HITS,
   OS_PROP41_VIOLATIONS, /* Prop. 4.1 checks that failed */
   OS_PROP41_CHECKS,
+  OS_UPDATES,
   OS_N
 };
 
@@ -102,6 +103,7 @@ typedef struct orc_table {
   uint32_t cap;        /* kick-out cap (walks), try cap (rattle), bin budget (search) */
   uint32_t rattle_tie_resident; /* debug reading: resident wins rattle ties */
   uint32_t hash_family;  /* 0: fmix32(key ^ seed_i); 1: fmix32(fmix32(key + seed_i) ^ seed_i*0x27D4EB2F) */
+  uint32_t spawn_k;      /* searches: spawns per round, their bins viewed together (Sec. 5); 1 = plain */
   uint64_t rng_seed;
   uint32_t seeds[4];
 
@@ -253,6 +255,7 @@ orc_table *orc_create(uint64_t n_bins, uint32_t B, uint32_t d, uint32_t policy,
   t->policy = policy & 0xFF;
   t->ghost = (policy & ORC_GHOST) ? 1 : 0;
   t->cap = cap;
+  t->spawn_k = 1;
   t->rng_seed = rng_seed;
   for (uint32_t i = 0; i < d; i++) t->seeds[i] = seeds[i];
   uint64_t ns = n_bins * B;
@@ -280,6 +283,11 @@ void orc_destroy(orc_table *t) {
 
 void orc_set_rattle_tie_resident(orc_table *t, int on) { t->rattle_tie_resident = on ? 1 : 0; }
 void orc_set_hash_family(orc_table *t, int f) { t->hash_family = f ? 1 : 0; }
+int orc_set_spawn_k(orc_table *t, uint32_t k) {
+  if (k < 1 || k > 8) return -1;
+  t->spawn_k = k;
+  return 0;
+}
 /* Fixtures: start a bin with a given spawn count (as left by earlier searches). */
 int orc_set_spawn(orc_table *t, uint64_t bin, uint32_t count) {
   if (bin >= t->n || count > 15) return -1;
@@ -635,6 +643,13 @@ static int pick_group(const orc_table *t) {
   return best;
 }
 
+static void mark_visited(orc_table *t, uint64_t bin) {
+  if (t->visited[bin]) return;
+  grow((void **)&t->visited_list, &t->visited_capacity, t->n_visited + 1, 8);
+  t->visited[bin] = 1;
+  t->visited_list[t->n_visited++] = bin;
+}
+
 static void push_group(orc_table *t, uint64_t bin, int32_t parent, int32_t pslot) {
   grow((void **)&t->groups, &t->groups_capacity, t->n_groups + 1, sizeof(group_t));
   group_t *g = &t->groups[t->n_groups++];
@@ -644,9 +659,7 @@ static void push_group(orc_table *t, uint64_t bin, int32_t parent, int32_t pslot
   g->next = 0;
   g->skey = t->spawn[bin];
   g->depth = parent < 0 ? 0 : t->groups[parent].depth + 1;
-  grow((void **)&t->visited_list, &t->visited_capacity, t->n_visited + 1, 8);
-  t->visited[bin] = 1;
-  t->visited_list[t->n_visited++] = bin;
+  mark_visited(t, bin);
 }
 
 static int insert_search(orc_table *t, uint64_t krec, const uint64_t *b) {
@@ -667,46 +680,67 @@ static int insert_search(orc_table *t, uint64_t krec, const uint64_t *b) {
   push_group(t, b0, -1, -1);
   push_group(t, b1, -1, -1);
   for (;;) {
-    int g = pick_group(t);
-    if (g < 0) return ORC_FAILED;                 /* nothing left to spawn */
-    uint64_t gb = t->groups[g].bin;
-    uint32_t s = t->groups[g].next++;
-    uint64_t r = t->rec[gb * t->B + s];
-    uint64_t y = other_bin(t, r, gb);
-    if (t->visited[y]) continue;
-    if ((t->policy == ORC_SORTED || t->policy == ORC_HYBRID) && t->spawn[gb] < 15) t->spawn[gb]++;
-    if (t->cur_viewed == t->cap) return ORC_FAILED; /* budget spent */
-    view(t);
-    int f = lowest_free(t, y);
-    int isdup = 0;
-    if (f < 0 && t->ghost) { f = lowest_dup(t, y); isdup = f >= 0; }
-    if (f >= 0) {
-      /* path from the root group to the spawned record */
-      uint32_t depth = 1;
-      for (int32_t q = g; t->groups[q].parent >= 0; q = t->groups[q].parent) depth++;
-      uint64_t *path_bin = (uint64_t *)xcalloc(depth, 8);
-      uint32_t *path_slot = (uint32_t *)xcalloc(depth, 4);
-      uint32_t len = 0;
-      path_bin[len] = gb; path_slot[len] = s; len++;
-      int32_t p = g;
-      while (t->groups[p].parent >= 0) {
-        path_bin[len] = t->groups[t->groups[p].parent].bin;
-        path_slot[len] = (uint32_t)t->groups[p].pslot;
-        len++;
-        p = t->groups[p].parent;
-      }
-      /* apply the chain from the root: the new key into the root slot, each
-       * displaced record into the next slot, the last into y */
-      uint64_t cur = krec;
-      for (uint32_t i = len; i-- > 0;) cur = kick(t, path_bin[i], path_slot[i], cur);
-      free(path_bin);
-      free(path_slot);
-      prop41_check(t, y);
-      if (isdup) evict_dup(t, y, (uint32_t)f, cur);
-      else put(t, y * t->B + f, cur, 0, 0);
-      return ORC_OK;
+    /* one round: up to spawn_k spawns in candidate order, their bins viewed
+     * together (Sec. 5: spawning the k best records at a time lets the
+     * fetches overlap); the first of them, in that order, with room ends
+     * the search, the others join as groups.  spawn_k = 1: the plain search. */
+    int rg[8];
+    uint32_t rs[8];
+    uint64_t ry[8];
+    uint32_t nr = 0;
+    int out = 0;  /* budget spent during the round */
+    while (nr < t->spawn_k) {
+      int g = pick_group(t);
+      if (g < 0) break;                              /* nothing left to spawn */
+      uint64_t gb = t->groups[g].bin;
+      uint32_t s = t->groups[g].next++;
+      uint64_t r = t->rec[gb * t->B + s];
+      uint64_t y = other_bin(t, r, gb);
+      if (t->visited[y]) continue;
+      if ((t->policy == ORC_SORTED || t->policy == ORC_HYBRID) && t->spawn[gb] < 15) t->spawn[gb]++;
+      if (t->cur_viewed == t->cap) { out = 1; break; } /* budget spent */
+      view(t);
+      mark_visited(t, y);
+      rg[nr] = g; rs[nr] = s; ry[nr] = y; nr++;
     }
-    push_group(t, y, g, (int32_t)s);
+    if (nr == 0) return ORC_FAILED;
+    for (uint32_t i = 0; i < nr; i++) {
+      int g = rg[i];
+      uint32_t s = rs[i];
+      uint64_t y = ry[i];
+      uint64_t gb = t->groups[g].bin;
+      int f = lowest_free(t, y);
+      int isdup = 0;
+      if (f < 0 && t->ghost) { f = lowest_dup(t, y); isdup = f >= 0; }
+      if (f >= 0) {
+        /* path from the root group to the spawned record */
+        uint32_t depth = 1;
+        for (int32_t q = g; t->groups[q].parent >= 0; q = t->groups[q].parent) depth++;
+        uint64_t *path_bin = (uint64_t *)xcalloc(depth, 8);
+        uint32_t *path_slot = (uint32_t *)xcalloc(depth, 4);
+        uint32_t len = 0;
+        path_bin[len] = gb; path_slot[len] = s; len++;
+        int32_t p = g;
+        while (t->groups[p].parent >= 0) {
+          path_bin[len] = t->groups[t->groups[p].parent].bin;
+          path_slot[len] = (uint32_t)t->groups[p].pslot;
+          len++;
+          p = t->groups[p].parent;
+        }
+        /* apply the chain from the root: the new key into the root slot, each
+         * displaced record into the next slot, the last into y */
+        uint64_t cur = krec;
+        for (uint32_t j = len; j-- > 0;) cur = kick(t, path_bin[j], path_slot[j], cur);
+        free(path_bin);
+        free(path_slot);
+        prop41_check(t, y);
+        if (isdup) evict_dup(t, y, (uint32_t)f, cur);
+        else put(t, y * t->B + f, cur, 0, 0);
+        return ORC_OK;
+      }
+    }
+    for (uint32_t i = 0; i < nr; i++) push_group(t, ry[i], rg[i], (int32_t)rs[i]);
+    if (out) return ORC_FAILED;
   }
 }
 
@@ -733,36 +767,52 @@ static int insert_search_dary(orc_table *t, uint64_t krec, const uint64_t *b) {
   t->n_groups = 0;
   for (uint32_t i = 0; i < t->d; i++) push_group(t, b[i], -1, -1);
   for (;;) {
-    int g = pick_group(t);
-    if (g < 0) return ORC_FAILED;                 /* nothing left to try */
-    uint64_t gb = t->groups[g].bin;
-    uint32_t j = t->groups[g].next++;
-    uint64_t r = t->rec[gb];
-    uint64_t rb[4];
-    bins_of(t, key_of(r), rb);
-    uint64_t y = rb[j];
-    if (y == gb || t->visited[y]) continue;
-    if ((t->policy == ORC_SORTED || t->policy == ORC_HYBRID) && t->spawn[gb] < 15) t->spawn[gb]++;
-    if (t->cur_viewed == t->cap) return ORC_FAILED; /* budget spent */
-    view(t);
-    if (is_free(t, y)) {
-      /* the chain from the root bin: the new key into the root, each
-       * displaced record into the next bin of the path, the last into y */
-      uint32_t depth = 1;
-      for (int32_t q = g; t->groups[q].parent >= 0; q = t->groups[q].parent) depth++;
-      uint64_t *path = (uint64_t *)xcalloc(depth, 8);
-      uint32_t len = 0;
-      for (int32_t q = g; q >= 0; q = t->groups[q].parent) path[len++] = t->groups[q].bin;
-      uint64_t cur = krec;
-      for (uint32_t i = len; i-- > 0;) {
-        cur = put(t, path[i], cur, 0, 0);
-        t->cur_kicks++;
-      }
-      free(path);
-      put(t, y, cur, 0, 0);
-      return ORC_OK;
+    /* rounds of spawn_k tries, as in the two-choice searches */
+    int rg[8];
+    uint32_t rj[8];
+    uint64_t ry[8];
+    uint32_t nr = 0;
+    int out = 0;
+    while (nr < t->spawn_k) {
+      int g = pick_group(t);
+      if (g < 0) break;                              /* nothing left to try */
+      uint64_t gb = t->groups[g].bin;
+      uint32_t j = t->groups[g].next++;
+      uint64_t r = t->rec[gb];
+      uint64_t rb[4];
+      bins_of(t, key_of(r), rb);
+      uint64_t y = rb[j];
+      if (y == gb || t->visited[y]) continue;
+      if ((t->policy == ORC_SORTED || t->policy == ORC_HYBRID) && t->spawn[gb] < 15) t->spawn[gb]++;
+      if (t->cur_viewed == t->cap) { out = 1; break; } /* budget spent */
+      view(t);
+      mark_visited(t, y);
+      rg[nr] = g; rj[nr] = j; ry[nr] = y; nr++;
     }
-    push_group(t, y, g, (int32_t)j);
+    if (nr == 0) return ORC_FAILED;
+    for (uint32_t i = 0; i < nr; i++) {
+      int g = rg[i];
+      uint64_t y = ry[i];
+      if (is_free(t, y)) {
+        /* the chain from the root bin: the new key into the root, each
+         * displaced record into the next bin of the path, the last into y */
+        uint32_t depth = 1;
+        for (int32_t q = g; t->groups[q].parent >= 0; q = t->groups[q].parent) depth++;
+        uint64_t *path = (uint64_t *)xcalloc(depth, 8);
+        uint32_t len = 0;
+        for (int32_t q = g; q >= 0; q = t->groups[q].parent) path[len++] = t->groups[q].bin;
+        uint64_t cur = krec;
+        for (uint32_t j = len; j-- > 0;) {
+          cur = put(t, path[j], cur, 0, 0);
+          t->cur_kicks++;
+        }
+        free(path);
+        put(t, y, cur, 0, 0);
+        return ORC_OK;
+      }
+    }
+    for (uint32_t i = 0; i < nr; i++) push_group(t, ry[i], rg[i], (int32_t)rj[i]);
+    if (out) return ORC_FAILED;
   }
 }
 
@@ -926,6 +976,36 @@ void orc_delete_batch(orc_table *t, const uint32_t *keys, uint64_t n, uint8_t *f
       if (was_ghost) t->stats[OS_LIVE_GHOSTS]--;
     }
     if (found) found[i] = (uint8_t)f;
+  }
+}
+
+/* Insert with the absent-key assumption of Sec. 3 lifted (upsert): a key
+ * already present gets the new value in every copy (a ghost pair keeps its
+ * duplicate marks) and status 5; an absent key is inserted as by
+ * orc_insert_batch.  Keys are taken in order, so a key repeated in the batch
+ * is inserted once and then updated. */
+void orc_upsert_batch(orc_table *t, const uint32_t *keys, const uint32_t *vals, uint64_t n, uint8_t *status) {
+  for (uint64_t i = 0; i < n; i++) {
+    uint64_t b[4];
+    int f = 0;
+    if (keys[i] != ORC_RESERVED_KEY) {
+      bins_of(t, keys[i], b);
+      for (uint32_t j = 0; j < t->d; j++)
+        for (uint32_t s = 0; s < t->B; s++) {
+          uint64_t slot = b[j] * t->B + s;
+          if (t->rec[slot] != ORC_EMPTY && key_of(t->rec[slot]) == keys[i]) {
+            t->rec[slot] = ((uint64_t)keys[i] << 32) | vals[i];
+            f = 1;
+          }
+        }
+    }
+    if (f) {
+      t->stats[OS_UPDATES]++;
+      if (status) status[i] = 5;
+      continue;
+    }
+    int st = insert_one(t, keys[i], vals[i], NULL, NULL);
+    if (status) status[i] = (uint8_t)st;
   }
 }
 

@@ -18,7 +18,7 @@ from . import build as _build
 # return codes
 OK, EINVAL, ENOMEM, ECUDA, EBUSY, ENOTSUP = 0, -1, -2, -3, -4, -5
 # per-key insert status
-ST_OK, ST_FAILED, ST_ABORTED, ST_INVALID = 0, 1, 2, 3
+ST_OK, ST_FAILED, ST_ABORTED, ST_INVALID, ST_UPDATED = 0, 1, 2, 3, 5
 CHAIN_BUCKETS = 40  # CK_CHAIN_BUCKETS
 # policies (Sec. 3-7) and the ghost flag (Sec. 4)
 RANDOM, BFS, SORTED, QUEUE, RATTLE, HYBRID = 0, 1, 2, 3, 4, 5
@@ -27,7 +27,8 @@ GHOST = 0x100
 PARAM_CHAIN_CAP, PARAM_MAX_RETRIES, PARAM_RNG_SEED = 1, 2, 3
 PARAM_HASH_SEED0, PARAM_BLOCK = 10, 20
 PARAM_RATTLE_TIE_RESIDENT, PARAM_ORDERED_WRITES, PARAM_OVERLAP, PARAM_HASH_FAMILY = 30, 31, 32, 33
-INS_SERIAL = 1
+PARAM_SPAWN_K = 34
+INS_SERIAL, INS_UPSERT = 1, 2
 HIST_BUCKETS = 200
 
 POLICY_NAMES = {"random": RANDOM, "bfs": BFS, "sorted": SORTED, "queue": QUEUE, "rattle": RATTLE,
@@ -41,7 +42,7 @@ class CkStats(ctypes.Structure):
         "lookup_hits", "deletes", "delete_hits", "delete_aborts", "conflict_views", "bins_viewed_all",
         "total_slots")] + [
         ("load", ctypes.c_double), ("bins_viewed_per_insert", ctypes.c_double),
-        ("aborts_per_insert", ctypes.c_double)]
+        ("aborts_per_insert", ctypes.c_double), ("updates", ctypes.c_uint64)]
 
 
 _lib = None
@@ -174,14 +175,14 @@ class CuckooTable:
         _check(load().ck_set_param(self._h, key, int(value)), "ck_set_param")
 
     # ---- batch operations ----
-    def insert(self, keys, vals, status=None, viewed=None, serial=False, stream=None):
+    def insert(self, keys, vals, status=None, viewed=None, serial=False, stream=None, upsert=False):
         keys, vals = _u32_view(keys), _u32_view(vals)
         n = keys.numel()
         if vals.numel() != n:
             raise ValueError("keys and values differ in length")
         if status is None:
             status = torch.empty(n, dtype=torch.uint8, device=keys.device)
-        flags = INS_SERIAL if serial else 0
+        flags = (INS_SERIAL if serial else 0) | (INS_UPSERT if upsert else 0)
         rc = load().ck_insert_batch_ex(self._h, _ptr(keys), _ptr(vals), n, _ptr(status), _ptr(viewed),
                                        flags, _stream(stream))
         _check(rc, "ck_insert_batch")

@@ -48,13 +48,15 @@ constexpr uint32_t VER_ONE = 1u << VER_SHIFT;
 enum Policy : uint32_t { P_RANDOM = 0, P_BFS = 1, P_SORTED = 2, P_QUEUE = 3, P_RATTLE = 4, P_HYBRID = 5 };
 // ST_CONFLICT: a claim lost a race, retry; ST_LONG: the local plan is full,
 // continue with a scratch-backed plan.
-enum Status : int { ST_OK = 0, ST_FAILED = 1, ST_ABORTED = 2, ST_INVALID = 3, ST_CONFLICT = 100, ST_LONG = 101 };
+enum Status : int {
+  ST_OK = 0, ST_FAILED = 1, ST_ABORTED = 2, ST_INVALID = 3, ST_UPDATED = 5, ST_CONFLICT = 100, ST_LONG = 101
+};
 
 // device counters (uint64 each)
 enum Counter : int {
   C_INS_OK = 0, C_INS_FAILED, C_INS_ABORTED, C_VIEWED, C_KICKS, C_CHAIN_MAX, C_ABORTS,
   C_GHOSTS_MADE, C_DUP_EVICT, C_SIZE, C_LIVE_GHOSTS /* C_SIZE + 1 */, C_LOOKUPS, C_LOOKUP_HITS, C_DELETES,
-  C_DELETE_HITS, C_DELETE_ABORTS, C_REVIEWS, C_VIEWED_ALL, C_N = 24
+  C_DELETE_HITS, C_DELETE_ABORTS, C_REVIEWS, C_VIEWED_ALL, C_UPDATES, C_N = 24
 };
 constexpr int HIST_BUCKETS = 200;
 // chain-length histogram of successful insertions: kick-outs k < 32 exact,
@@ -91,6 +93,7 @@ struct DevTable {
   uint32_t n_searchers;
   uint32_t n_long;
   uint32_t hash_family;          // 0: fmix32(k ^ seed_i); 1: decorrelated (see bin_hash)
+  uint32_t spawn_k;              // searches: spawns per round, their bins fetched together (1..8)
   uint32_t seeds[4];
 };
 

@@ -105,6 +105,145 @@ __device__ __forceinline__ int insert_one(const DevTable& t, Ctx& c, uint8_t* re
   return st;
 }
 
+// ------------------------------------------------------------------
+// deletes (Sec. 1): every copy goes, each under its claim flag (Sec. 8)
+// ------------------------------------------------------------------
+// The copies a delete removes (at most d bins of B slots).
+struct DelPlan {
+  uint32_t bin[16];
+  uint8_t slot[16];
+  uint8_t old_r[16];  // two-choice: duplicate mark; d-ary: rattle counter
+  int n;
+};
+
+// One delete: find the key in its bins and claim the slots holding it
+// (every copy: a ghost pair has two), clear them, release.  A miss is
+// reported only when the bins were seen unclaimed and unchanged across the
+// read (unchanged_since), so a delete running beside insertions on another
+// stream never misses a key that is being moved.  Slots claimed by a
+// writer are waited out with backoff, at most DELETE_ATTEMPTS times
+// (status 2).
+constexpr int DELETE_ATTEMPTS = 1024;
+
+template <int B>
+__device__ __forceinline__ int delete_one(const DevTable& t, uint32_t key, DelPlan& p, uint32_t& ghost_removed) {
+  uint32_t b[4];
+  bins_of(t, key, b);
+  const uint32_t nb = t.d;
+  constexpr uint32_t CLAIM_BITS = (1u << B) - 1;
+  for (int attempt = 0; attempt < DELETE_ATTEMPTS; attempt++) {
+    p.n = 0;
+    bool conflict = false, any = false;
+    int dup_copies = 0;
+    uint32_t seen[4];
+    for (uint32_t j = 0; j < nb && !conflict; j++) {
+      View<B> v;
+      load_view<B>(t, b[j], v);
+      uint32_t m = v.m;
+      seen[j] = m;
+      uint32_t add = 0;
+#pragma unroll
+      for (int s = 0; s < B; s++) {
+        if (v.s[s] != EMPTY && key_of(v.s[s]) == key) {
+          if ((m >> s) & 1u) { conflict = true; break; }  // a writer holds it
+          add |= 1u << s;
+        }
+      }
+      if (conflict || !add) continue;
+      if (!cas_acquire(t.meta + b[j], m, m + add)) { conflict = true; break; }
+      any = true;
+      for (int s = 0; s < B; s++) {
+        if ((add >> s) & 1u) {
+          int i = p.n++;
+          p.bin[i] = b[j];
+          p.slot[i] = (uint8_t)s;
+          p.old_r[i] = (uint8_t)((B == 1) ? rattle_of(m) : ((m >> (DUP_SHIFT + s)) & 1u));
+          dup_copies += (B > 1) ? p.old_r[i] : 0;
+        }
+      }
+    }
+    if (!conflict && !any) {
+      if (unchanged_since(t.meta, b, seen, nb, CLAIM_BITS)) return 0;
+      conflict = true;  // a writer was active in the key's bins: look again
+    }
+    if (conflict) {
+      for (int i = 0; i < p.n; i++) add_relaxed(t.meta + p.bin[i], 0u - (1u << p.slot[i]));
+      p.n = 0;
+      uint32_t w = 128u << (attempt < 13 ? attempt : 13);
+      __nanosleep(w + (fmix32(key ^ attempt) & (w - 1)));
+      continue;
+    }
+    for (int i = 0; i < p.n; i++) st_slot(t.slots + (uint64_t)p.bin[i] * B + p.slot[i], EMPTY);
+    for (int i = 0; i < p.n; i++) {
+      uint32_t delta = VER_ONE - (1u << p.slot[i]);
+      if (B == 1) delta -= (uint32_t)p.old_r[i] << RATTLE_SHIFT;        // the bin forgets r(x)
+      else if (p.old_r[i]) delta -= 1u << (DUP_SHIFT + p.slot[i]);       // duplicate mark goes too
+      add_release(t.meta + p.bin[i], delta);
+    }
+    ghost_removed += dup_copies >= 2 ? 1 : 0;
+    return 1;
+  }
+  return 2;
+}
+
+// Overwrite the value of a present key (CK_INS_UPSERT): claim every slot
+// holding it (both copies of a ghost pair), store the new record, release
+// with a version bump; the duplicate marks stay.  Returns 1 if updated, 0 if
+// the key is absent (a miss proven as delete_one proves it), 2 if claimed
+// slots were not released within DELETE_ATTEMPTS tries.
+template <int B>
+__device__ __forceinline__ int update_one(const DevTable& t, uint32_t key, uint64_t rec, DelPlan& p) {
+  uint32_t b[4];
+  bins_of(t, key, b);
+  const uint32_t nb = t.d;
+  constexpr uint32_t CLAIM_BITS = (1u << B) - 1;
+  for (int attempt = 0; attempt < DELETE_ATTEMPTS; attempt++) {
+    p.n = 0;
+    bool conflict = false, any = false;
+    uint32_t seen[4];
+    for (uint32_t j = 0; j < nb && !conflict; j++) {
+      View<B> v;
+      load_view<B>(t, b[j], v);
+      uint32_t m = v.m;
+      seen[j] = m;
+      uint32_t add = 0;
+#pragma unroll
+      for (int s = 0; s < B; s++) {
+        if (v.s[s] != EMPTY && key_of(v.s[s]) == key) {
+          if ((m >> s) & 1u) { conflict = true; break; }  // a writer holds it
+          add |= 1u << s;
+        }
+      }
+      if (conflict || !add) continue;
+      if (!cas_acquire(t.meta + b[j], m, m + add)) { conflict = true; break; }
+      any = true;
+      for (int s = 0; s < B; s++) {
+        if ((add >> s) & 1u) {
+          int i = p.n++;
+          p.bin[i] = b[j];
+          p.slot[i] = (uint8_t)s;
+        }
+      }
+    }
+    if (!conflict && !any) {
+      if (unchanged_since(t.meta, b, seen, nb, CLAIM_BITS)) return 0;
+      conflict = true;
+    }
+    if (conflict) {
+      for (int i = 0; i < p.n; i++) add_relaxed(t.meta + p.bin[i], 0u - (1u << p.slot[i]));
+      p.n = 0;
+      uint32_t w = 128u << (attempt < 13 ? attempt : 13);
+      __nanosleep(w + (fmix32(key ^ attempt) & (w - 1)));
+      continue;
+    }
+    for (int i = 0; i < p.n; i++) st_slot(t.slots + (uint64_t)p.bin[i] * B + p.slot[i], rec);
+    fence_release();
+    for (int i = 0; i < p.n; i++) red_relaxed(t.meta + p.bin[i], VER_ONE - (1u << p.slot[i]));
+    return 1;
+  }
+  return 2;
+}
+
 // Insert kernel.  Concurrent mode: each block takes a contiguous range of
 // the batch and its threads pull keys from it, one insertion per thread at
 // a time, plans in local memory.  Serial mode (SERIAL, one
@@ -124,7 +263,8 @@ template <int B, int POL, bool GHOST, bool SERIAL>
 __global__ void __launch_bounds__(256, 4) k_insert(DevTable t, const uint32_t* __restrict__ keys,
                                                 const uint32_t* __restrict__ vals, uint64_t n,
                                                 uint8_t* __restrict__ status,
-                                                uint32_t* __restrict__ viewed_out, uint64_t load_base) {
+                                                uint32_t* __restrict__ viewed_out, uint64_t load_base,
+                                                uint32_t upsert) {
   asm volatile("griddepcontrol.launch_dependents;");
   __shared__ unsigned int h_views[HIST_BUCKETS];
   __shared__ unsigned int h_cnt[HIST_BUCKETS];
@@ -166,7 +306,7 @@ __global__ void __launch_bounds__(256, 4) k_insert(DevTable t, const uint32_t* _
 
   // per-thread tallies of one launch (32-bit: a thread handles far fewer
   // than 2^32 keys or bin views in one launch), flushed into 64-bit counters
-  uint32_t ok = 0, failed = 0, aborted = 0, viewed = 0, kicks = 0, ghosts = 0, dupev = 0;
+  uint32_t ok = 0, failed = 0, aborted = 0, viewed = 0, kicks = 0, ghosts = 0, dupev = 0, updates = 0;
   uint32_t reviews = 0, viewed_all = 0;
   uint32_t aborts = 0, chain_max = 0;
   for (;;) {
@@ -181,6 +321,17 @@ __global__ void __launch_bounds__(256, 4) k_insert(DevTable t, const uint32_t* _
     Ctx c;
     c.key = key;
     c.krec = ((uint64_t)key << 32) | vals[i];
+    if (upsert) {  // a present key is overwritten in place, not inserted again
+      DelPlan up;
+      int r = update_one<B>(t, key, c.krec, up);
+      if (r != 0) {
+        updates += r == 1;
+        aborted += r == 2;
+        if (status) status[i] = (uint8_t)(r == 1 ? ST_UPDATED : ST_ABORTED);
+        if (viewed_out) viewed_out[i] = 0;
+        continue;
+      }
+    }
     c.viewed = 0;
     c.reviews = 0;
     // concurrent mode retries a failed attempt (up to three times): other
@@ -223,6 +374,7 @@ __global__ void __launch_bounds__(256, 4) k_insert(DevTable t, const uint32_t* _
   flush_counter(&bc[C_DUP_EVICT], dupev);
   flush_counter(&bc[C_REVIEWS], reviews);
   flush_counter(&bc[C_VIEWED_ALL], viewed_all);
+  flush_counter(&bc[C_UPDATES], updates);
   if (chain_max) atomicMax(&bc[C_CHAIN_MAX], (unsigned long long)chain_max);
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -367,87 +519,6 @@ static __global__ void __launch_bounds__(256) k_lookup_dary(DevTable t, const ui
     if (hits_sh) atomicAdd(t.counters + C_LOOKUP_HITS, hits_sh);
     if (cnt_sh) atomicAdd(t.counters + C_LOOKUPS, cnt_sh);
   }
-}
-
-// ------------------------------------------------------------------
-// deletes (Sec. 1): every copy goes, each under its claim flag (Sec. 8)
-// ------------------------------------------------------------------
-// The copies a delete removes (at most d bins of B slots).
-struct DelPlan {
-  uint32_t bin[16];
-  uint8_t slot[16];
-  uint8_t old_r[16];  // two-choice: duplicate mark; d-ary: rattle counter
-  int n;
-};
-
-// One delete: find the key in its bins and claim the slots holding it
-// (every copy: a ghost pair has two), clear them, release.  A miss is
-// reported only when the bins were seen unclaimed and unchanged across the
-// read (unchanged_since), so a delete running beside insertions on another
-// stream never misses a key that is being moved.  Slots claimed by a
-// writer are waited out with backoff, at most DELETE_ATTEMPTS times
-// (status 2).
-constexpr int DELETE_ATTEMPTS = 1024;
-
-template <int B>
-__device__ __forceinline__ int delete_one(const DevTable& t, uint32_t key, DelPlan& p, uint32_t& ghost_removed) {
-  uint32_t b[4];
-  bins_of(t, key, b);
-  const uint32_t nb = t.d;
-  constexpr uint32_t CLAIM_BITS = (1u << B) - 1;
-  for (int attempt = 0; attempt < DELETE_ATTEMPTS; attempt++) {
-    p.n = 0;
-    bool conflict = false, any = false;
-    int dup_copies = 0;
-    uint32_t seen[4];
-    for (uint32_t j = 0; j < nb && !conflict; j++) {
-      View<B> v;
-      load_view<B>(t, b[j], v);
-      uint32_t m = v.m;
-      seen[j] = m;
-      uint32_t add = 0;
-#pragma unroll
-      for (int s = 0; s < B; s++) {
-        if (v.s[s] != EMPTY && key_of(v.s[s]) == key) {
-          if ((m >> s) & 1u) { conflict = true; break; }  // a writer holds it
-          add |= 1u << s;
-        }
-      }
-      if (conflict || !add) continue;
-      if (!cas_acquire(t.meta + b[j], m, m + add)) { conflict = true; break; }
-      any = true;
-      for (int s = 0; s < B; s++) {
-        if ((add >> s) & 1u) {
-          int i = p.n++;
-          p.bin[i] = b[j];
-          p.slot[i] = (uint8_t)s;
-          p.old_r[i] = (uint8_t)((B == 1) ? rattle_of(m) : ((m >> (DUP_SHIFT + s)) & 1u));
-          dup_copies += (B > 1) ? p.old_r[i] : 0;
-        }
-      }
-    }
-    if (!conflict && !any) {
-      if (unchanged_since(t.meta, b, seen, nb, CLAIM_BITS)) return 0;
-      conflict = true;  // a writer was active in the key's bins: look again
-    }
-    if (conflict) {
-      for (int i = 0; i < p.n; i++) add_relaxed(t.meta + p.bin[i], 0u - (1u << p.slot[i]));
-      p.n = 0;
-      uint32_t w = 128u << (attempt < 13 ? attempt : 13);
-      __nanosleep(w + (fmix32(key ^ attempt) & (w - 1)));
-      continue;
-    }
-    for (int i = 0; i < p.n; i++) st_slot(t.slots + (uint64_t)p.bin[i] * B + p.slot[i], EMPTY);
-    for (int i = 0; i < p.n; i++) {
-      uint32_t delta = VER_ONE - (1u << p.slot[i]);
-      if (B == 1) delta -= (uint32_t)p.old_r[i] << RATTLE_SHIFT;        // the bin forgets r(x)
-      else if (p.old_r[i]) delta -= 1u << (DUP_SHIFT + p.slot[i]);       // duplicate mark goes too
-      add_release(t.meta + p.bin[i], delta);
-    }
-    ghost_removed += dup_copies >= 2 ? 1 : 0;
-    return 1;
-  }
-  return 2;
 }
 
 template <int B>

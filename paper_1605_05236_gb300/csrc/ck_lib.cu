@@ -139,7 +139,8 @@ int init_table(ck_table* t, void* buf, size_t bytes, bool owns, uint64_t bins, u
   dt.ghost = (policy & CK_GHOST) ? 1 : 0;
   dt.cap = 500;
   dt.max_retries = 64;
-  dt.ordered_writes = 1;
+  dt.ordered_writes = 0;  // see CK_PARAM_ORDERED_WRITES
+  dt.spawn_k = 1;
   dt.tie_resident = 0;
   dt.n_searchers = is_search(policy) ? searchers_for(bins) : 0;
   dt.seeds[0] = 0x9E3779B9u;
@@ -165,9 +166,9 @@ int init_table(ck_table* t, void* buf, size_t bytes, bool owns, uint64_t bins, u
 template <int B, int POL, bool GHOST>
 cudaError_t launch_insert_dt(const DevTable& dt, uint32_t block, int sm_count, bool overlap, uint64_t load_base,
                              const uint32_t* keys, const uint32_t* vals, uint64_t n, uint8_t* st, uint32_t* viewed,
-                             bool serial, cudaStream_t s, uint64_t max_threads = ~0ull) {
+                             bool serial, cudaStream_t s, uint64_t max_threads = ~0ull, uint32_t upsert = 0) {
   if (serial) {
-    k_insert<B, POL, GHOST, true><<<1, 1, 0, s>>>(dt, keys, vals, n, st, viewed, load_base);
+    k_insert<B, POL, GHOST, true><<<1, 1, 0, s>>>(dt, keys, vals, n, st, viewed, load_base, upsert);
     return cudaGetLastError();
   }
   // persistent launch: at most the blocks that fit on the GPU at once
@@ -201,18 +202,18 @@ cudaError_t launch_insert_dt(const DevTable& dt, uint32_t block, int sm_count, b
   attr[0].val.programmaticStreamSerializationAllowed = overlap ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_insert<B, POL, GHOST, false>, dt, keys, vals, n, st, viewed, load_base);
+  return cudaLaunchKernelEx(&cfg, k_insert<B, POL, GHOST, false>, dt, keys, vals, n, st, viewed, load_base, upsert);
 }
 
 template <int B, int POL, bool GHOST>
 cudaError_t launch_insert(const ck_table* t, const uint32_t* keys, const uint32_t* vals, uint64_t n, uint8_t* st,
-                          uint32_t* viewed, bool serial, cudaStream_t s) {
+                          uint32_t* viewed, bool serial, uint32_t upsert, cudaStream_t s) {
   return launch_insert_dt<B, POL, GHOST>(t->dt, t->block, t->sm_count, t->overlap != 0, t->load_base, keys, vals,
-                                         n, st, viewed, serial, s);
+                                         n, st, viewed, serial, s, ~0ull, upsert);
 }
 
 using InsertFn = cudaError_t (*)(const ck_table*, const uint32_t*, const uint32_t*, uint64_t, uint8_t*,
-                                 uint32_t*, bool, cudaStream_t);
+                                 uint32_t*, bool, uint32_t, cudaStream_t);
 
 template <int B>
 InsertFn pick_two_choice(uint32_t pol, bool ghost) {
@@ -371,6 +372,10 @@ int ck_set_param(ck_table* t, int key, int64_t value) {
     case CK_PARAM_OVERLAP:
       t->overlap = value ? 1 : 0;
       return CK_OK;
+    case CK_PARAM_SPAWN_K:
+      if (value < 1 || value > 8) return CK_EINVAL;
+      d.spawn_k = (uint32_t)value;
+      return CK_OK;
     case CK_PARAM_HASH_FAMILY:
       if (value != 0 && value != 1) return CK_EINVAL;
       d.hash_family = (uint32_t)value;
@@ -390,10 +395,11 @@ int ck_insert_batch_ex(ck_table* t, const uint32_t* d_keys, const uint32_t* d_va
   if (!t) return CK_EINVAL;
   if (n == 0) return CK_OK;
   if (!d_keys || !d_vals) return CK_EINVAL;
-  if (flags & ~(uint32_t)CK_INS_SERIAL) return CK_EINVAL;
+  if (flags & ~(uint32_t)(CK_INS_SERIAL | CK_INS_UPSERT)) return CK_EINVAL;
   InsertFn fn = pick_insert(t);
   if (!fn) return CK_ENOTSUP;
-  cudaError_t e = fn(t, d_keys, d_vals, n, d_status, d_viewed, (flags & CK_INS_SERIAL) != 0, S(stream));
+  cudaError_t e = fn(t, d_keys, d_vals, n, d_status, d_viewed, (flags & CK_INS_SERIAL) != 0,
+                     (flags & CK_INS_UPSERT) ? 1u : 0u, S(stream));
   t->last = S(stream);
   t->load_base += n;
   return check(e);
@@ -459,6 +465,7 @@ int ck_stats(ck_table* t, ck_stats_t* out) {
   uint64_t ins = out->inserts_ok + out->inserts_failed + out->inserts_aborted;
   out->bins_viewed_per_insert = ins ? (double)out->bins_viewed / (double)ins : 0.0;
   out->aborts_per_insert = ins ? (double)out->aborts / (double)ins : 0.0;
+  out->updates = c[C_UPDATES];
   return CK_OK;
 }
 

@@ -382,7 +382,8 @@ int ck_multi_create_on(ck_multi** out, void* dev_buf, size_t bytes, const ck_mul
     t.ghost = (policy & CK_GHOST) ? 1 : 0;
     t.cap = m->cap;
     t.max_retries = 64;
-    t.ordered_writes = 1;
+    t.ordered_writes = 0;
+    t.spawn_k = 1;
     t.n_searchers = 0;
     t.n_long = MULTI_LONG_PLANS;
     t.hash_family = 0;

@@ -43,6 +43,15 @@ constexpr size_t SEARCH_REGION = 16 + MAX_GROUPS * sizeof(Group) + VISITED_SLOTS
 
 __device__ __forceinline__ uint32_t vis_hash(uint32_t bin) { return (bin * 0x9E3779B1u) >> (32 - 10); }
 
+// Bring a bin's slots and metadata word toward L2 ahead of its view.
+template <int B>
+__device__ __forceinline__ void prefetch_bin(const DevTable& t, uint32_t bin) {
+  const uint64_t* p = t.slots + (uint64_t)bin * B;
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+  if (B == 8) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + 4));
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(t.meta + bin));
+}
+
 // Insert `bin` into the visited set; returns false if it was already there.
 __device__ __forceinline__ bool vis_insert(uint64_t* vis, uint32_t gen, uint32_t bin) {
   uint64_t tag = ((uint64_t)gen << 32) | bin;
@@ -126,86 +135,105 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
   push(b1, v1.m, ~0u);
 
   for (;;) {
-    // pick the group to pop from
-    while (head < ng && G[head].next >= B) head++;
-    if (head == ng) return c.foreign ? ST_CONFLICT : ST_FAILED;  // nothing left to spawn
-    uint32_t g = head;
-    if (ORDER != P_BFS) {
-      uint32_t best = G[head].key;
-      for (uint32_t q = head + 1; q < ng; q++) {
-        Group gq = G[q];
-        if (gq.next < B && gq.key < best) { best = gq.key; g = q; }
-      }
-    }
-    Group gr = G[g];
-    uint32_t s = gr.next;
-    G[g].next = (uint8_t)(s + 1);
-    if ((gr.meta >> s) & 1u) {  // claimed by another insertion: ignore it (Sec. 8)
-      c.foreign = 1;
-      continue;
-    }
-    uint64_t rec = ld_slot(t.slots + (uint64_t)gr.bin * B + s);
-    if (rec == EMPTY) continue;
-    uint32_t y = other_bin2(t, rec, gr.bin);
-    if (vis_has(vis, gen, y)) continue;
-    if (ORDER != P_BFS && spawn_of(gr.meta) < 15) {
-      uint32_t nm = gr.meta + (1u << SPAWN_SHIFT);
-      if (cas_acquire(t.meta + gr.bin, gr.meta, nm)) {
-        G[g].meta = nm;
-      } else {
-        G[g].stale = 1;
-        uint32_t m = ld_acquire(t.meta + gr.bin);
-        for (int k = 0; k < 64 && spawn_of(m) < 15; k++) {  // bounded: a lost count is harmless
-          if (cas_acquire(t.meta + gr.bin, m, m + (1u << SPAWN_SHIFT))) break;
-          m = ld_acquire(t.meta + gr.bin);
+    // one round: up to spawn_k spawns in candidate order, their bins
+    // prefetched together (Sec. 5: spawning the k best records at a time
+    // lets the fetches overlap); the first of them with room ends the
+    // search, the others join as groups.  spawn_k = 1: the plain search.
+    uint32_t rg[8], ry[8];
+    uint8_t rs[8];
+    uint32_t nr = 0;
+    bool out = false;  // budget spent during the round
+    while (nr < t.spawn_k) {
+      while (head < ng && G[head].next >= B) head++;
+      if (head == ng) break;  // nothing left to spawn
+      uint32_t g = head;
+      if (ORDER != P_BFS) {
+        uint32_t best = G[head].key;
+        for (uint32_t q = head + 1; q < ng; q++) {
+          Group gq = G[q];
+          if (gq.next < B && gq.key < best) { best = gq.key; g = q; }
         }
       }
-    }
-    if (c.viewed - c.viewed0 >= t.cap || ng >= MAX_GROUPS)  // budget spent
-      return c.foreign ? ST_CONFLICT : ST_FAILED;
-    View<B> vy;
-    load_view<B>(t, y, vy);
-    c.viewed++;
-    if (claimed_mask<B>(vy)) c.foreign = 1;
-    uint32_t fm = free_mask<B>(vy);
-    int term = lowest(fm);
-    bool isdup = false;
-    if (term < 0 && GHOST) {
-      term = lowest(dup_mask<B>(vy));
-      isdup = term >= 0;
-    }
-    if (term < 0) {
-      push(y, vy.m, (g << 3) | s);
-      continue;
-    }
-    // path root -> ... -> (g, s): depth entries in chain order
-    uint32_t depth = 1;
-    for (uint32_t q = g; G[q].parent != ~0u; q = G[q].parent >> 3) depth++;
-    if ((int)depth + 4 > c.pcap) return ST_LONG;
-    {
-      // entries in chain order; the group index rides in the content word
-      // until the slot is claimed
-      uint32_t q = g, qs = s;
-      for (int i = (int)depth - 1; i >= 0; i--) {
-        set_entry(c, i, pack_entry(G[q].bin, (int)qs, K_MOVE, false, 0, 0), q);
-        uint32_t par = G[q].parent;
-        if (par != ~0u) { qs = par & 7u; q = par >> 3; }
+      Group gr = G[g];
+      uint32_t s = gr.next;
+      G[g].next = (uint8_t)(s + 1);
+      if ((gr.meta >> s) & 1u) {  // claimed by another insertion: ignore it (Sec. 8)
+        c.foreign = 1;
+        continue;
       }
+      uint64_t rec = ld_slot(t.slots + (uint64_t)gr.bin * B + s);
+      if (rec == EMPTY) continue;
+      uint32_t y = other_bin2(t, rec, gr.bin);
+      if (vis_has(vis, gen, y)) continue;
+      if (ORDER != P_BFS && spawn_of(gr.meta) < 15) {
+        uint32_t nm = gr.meta + (1u << SPAWN_SHIFT);
+        if (cas_acquire(t.meta + gr.bin, gr.meta, nm)) {
+          G[g].meta = nm;
+        } else {
+          G[g].stale = 1;
+          uint32_t m = ld_acquire(t.meta + gr.bin);
+          for (int k = 0; k < 64 && spawn_of(m) < 15; k++) {  // bounded: a lost count is harmless
+            if (cas_acquire(t.meta + gr.bin, m, m + (1u << SPAWN_SHIFT))) break;
+            m = ld_acquire(t.meta + gr.bin);
+          }
+        }
+      }
+      if (c.viewed - c.viewed0 >= t.cap || ng + nr >= MAX_GROUPS) { out = true; break; }  // budget spent
+      vis_insert(vis, gen, y);
+      c.viewed++;
+      prefetch_bin<B>(t, y);
+      rg[nr] = g;
+      rs[nr] = (uint8_t)s;
+      ry[nr] = y;
+      nr++;
     }
-    // claim the path in chain order; each CAS checks its bin is as viewed,
-    // so the record read after the claim is the one the search saw
-    c.pn = 0;
-    for (uint32_t i = 0; i < depth; i++) {
-      Group gq = G[(uint32_t)content_at(c, (int)i)];
-      uint32_t sl = e_slot(desc_at(c, (int)i));
-      if (gq.stale) return ST_CONFLICT;
-      if (!cas_acquire(t.meta + gq.bin, gq.meta, gq.meta + (1u << sl))) return ST_CONFLICT;
-      c.pn = (int)i + 1;
-      set_content(c, (int)i, ld_slot(t.slots + (uint64_t)gq.bin * B + sl));
+    if (nr == 0) return c.foreign ? ST_CONFLICT : ST_FAILED;
+    for (uint32_t i = 0; i < nr; i++) {
+      const uint32_t g = rg[i], s = rs[i], y = ry[i];
+      View<B> vy;
+      load_view<B>(t, y, vy);
+      if (claimed_mask<B>(vy)) c.foreign = 1;
+      uint32_t fm = free_mask<B>(vy);
+      int term = lowest(fm);
+      bool isdup = false;
+      if (term < 0 && GHOST) {
+        term = lowest(dup_mask<B>(vy));
+        isdup = term >= 0;
+      }
+      if (term < 0) {
+        push(y, vy.m, (g << 3) | s);
+        continue;
+      }
+      // path root -> ... -> (g, s): depth entries in chain order
+      uint32_t depth = 1;
+      for (uint32_t q = g; G[q].parent != ~0u; q = G[q].parent >> 3) depth++;
+      if ((int)depth + 4 > c.pcap) return ST_LONG;
+      {
+        // entries in chain order; the group index rides in the content word
+        // until the slot is claimed
+        uint32_t q = g, qs = s;
+        for (int e = (int)depth - 1; e >= 0; e--) {
+          set_entry(c, e, pack_entry(G[q].bin, (int)qs, K_MOVE, false, 0, 0), q);
+          uint32_t par = G[q].parent;
+          if (par != ~0u) { qs = par & 7u; q = par >> 3; }
+        }
+      }
+      // claim the path in chain order; each CAS checks its bin is as viewed,
+      // so the record read after the claim is the one the search saw
+      c.pn = 0;
+      for (uint32_t e = 0; e < depth; e++) {
+        Group gq = G[(uint32_t)content_at(c, (int)e)];
+        uint32_t sl = e_slot(desc_at(c, (int)e));
+        if (gq.stale) return ST_CONFLICT;
+        if (!cas_acquire(t.meta + gq.bin, gq.meta, gq.meta + (1u << sl))) return ST_CONFLICT;
+        c.pn = (int)e + 1;
+        set_content(c, (int)e, ld_slot(t.slots + (uint64_t)gq.bin * B + sl));
+      }
+      c.kicks = depth;
+      if (isdup) return take_dup<B>(t, c, y, vy, term, false);
+      return take_free<B>(t, c, y, vy, term, false);
     }
-    c.kicks = depth;
-    if (isdup) return take_dup<B>(t, c, y, vy, term, false);
-    return take_free<B>(t, c, y, vy, term, false);
+    if (out) return c.foreign ? ST_CONFLICT : ST_FAILED;
   }
 }
 
@@ -257,75 +285,90 @@ __device__ int insert_search_dary(const DevTable& t, Ctx& c, uint8_t* region) {
   for (uint32_t i = 0; i < d; i++) push(b[i], v[i].m, ~0u);
 
   for (;;) {
-    while (head < ng && G[head].next >= d) head++;
-    if (head == ng) return c.foreign ? ST_CONFLICT : ST_FAILED;  // nothing left to try
-    uint32_t g = head;
-    if (ORDER != P_BFS) {
-      uint32_t best = G[head].key;
-      for (uint32_t q = head + 1; q < ng; q++) {
-        Group gq = G[q];
-        if (gq.next < d && gq.key < best) { best = gq.key; g = q; }
-      }
-    }
-    Group gr = G[g];
-    uint32_t j = gr.next;
-    G[g].next = (uint8_t)(j + 1);
-    if (gr.meta & 1u) {  // claimed by another insertion: ignore it (Sec. 8)
-      c.foreign = 1;
-      continue;
-    }
-    uint64_t rec = ld_slot(t.slots + gr.bin);
-    if (rec == EMPTY) continue;
-    uint32_t rb[4];
-    bins_of(t, key_of(rec), rb);
-    uint32_t y = rb[j];
-    if (y == gr.bin || vis_has(vis, gen, y)) continue;
-    if (ORDER != P_BFS && spawn_of(gr.meta) < 15) {
-      uint32_t nm = gr.meta + (1u << SPAWN_SHIFT);
-      if (cas_acquire(t.meta + gr.bin, gr.meta, nm)) {
-        G[g].meta = nm;
-      } else {
-        G[g].stale = 1;
-        uint32_t m = ld_acquire(t.meta + gr.bin);
-        for (int k = 0; k < 64 && spawn_of(m) < 15; k++) {  // bounded: a lost count is harmless
-          if (cas_acquire(t.meta + gr.bin, m, m + (1u << SPAWN_SHIFT))) break;
-          m = ld_acquire(t.meta + gr.bin);
+    // rounds of spawn_k tries, as in the two-choice searches
+    uint32_t rg[8], ry[8];
+    uint32_t nr = 0;
+    bool out = false;
+    while (nr < t.spawn_k) {
+      while (head < ng && G[head].next >= d) head++;
+      if (head == ng) break;  // nothing left to try
+      uint32_t g = head;
+      if (ORDER != P_BFS) {
+        uint32_t best = G[head].key;
+        for (uint32_t q = head + 1; q < ng; q++) {
+          Group gq = G[q];
+          if (gq.next < d && gq.key < best) { best = gq.key; g = q; }
         }
       }
-    }
-    if (c.viewed - c.viewed0 >= t.cap || ng >= MAX_GROUPS)  // budget spent
-      return c.foreign ? ST_CONFLICT : ST_FAILED;
-    View<1> vy;
-    load_view<1>(t, y, vy);
-    c.viewed++;
-    if (claimed_mask<1>(vy)) c.foreign = 1;
-    if (!free_mask<1>(vy)) {
-      push(y, vy.m, g << 3);
-      continue;
-    }
-    // path: root group -> ... -> group g, one record each, in chain order
-    uint32_t depth = 1;
-    for (uint32_t q = g; G[q].parent != ~0u; q = G[q].parent >> 3) depth++;
-    if ((int)depth + 4 > c.pcap) return ST_LONG;
-    {
-      uint32_t q = g;
-      for (int i = (int)depth - 1; i >= 0; i--) {
-        set_entry(c, i, pack_entry(G[q].bin, 0, K_MOVE, false, 0, 0), q);
-        if (G[q].parent != ~0u) q = G[q].parent >> 3;
+      Group gr = G[g];
+      uint32_t j = gr.next;
+      G[g].next = (uint8_t)(j + 1);
+      if (gr.meta & 1u) {  // claimed by another insertion: ignore it (Sec. 8)
+        c.foreign = 1;
+        continue;
       }
+      uint64_t rec = ld_slot(t.slots + gr.bin);
+      if (rec == EMPTY) continue;
+      uint32_t rb[4];
+      bins_of(t, key_of(rec), rb);
+      uint32_t y = rb[j];
+      if (y == gr.bin || vis_has(vis, gen, y)) continue;
+      if (ORDER != P_BFS && spawn_of(gr.meta) < 15) {
+        uint32_t nm = gr.meta + (1u << SPAWN_SHIFT);
+        if (cas_acquire(t.meta + gr.bin, gr.meta, nm)) {
+          G[g].meta = nm;
+        } else {
+          G[g].stale = 1;
+          uint32_t m = ld_acquire(t.meta + gr.bin);
+          for (int k = 0; k < 64 && spawn_of(m) < 15; k++) {  // bounded: a lost count is harmless
+            if (cas_acquire(t.meta + gr.bin, m, m + (1u << SPAWN_SHIFT))) break;
+            m = ld_acquire(t.meta + gr.bin);
+          }
+        }
+      }
+      if (c.viewed - c.viewed0 >= t.cap || ng + nr >= MAX_GROUPS) { out = true; break; }  // budget spent
+      vis_insert(vis, gen, y);
+      c.viewed++;
+      prefetch_bin<1>(t, y);
+      rg[nr] = g;
+      ry[nr] = y;
+      nr++;
     }
-    // claim the path in chain order from the metadata words as viewed; the
-    // record read after a claim is the one the search saw
-    c.pn = 0;
-    for (uint32_t i = 0; i < depth; i++) {
-      Group gq = G[(uint32_t)content_at(c, (int)i)];
-      if (gq.stale) return ST_CONFLICT;
-      if (!cas_acquire(t.meta + gq.bin, gq.meta, gq.meta + 1u)) return ST_CONFLICT;
-      c.pn = (int)i + 1;
-      set_content(c, (int)i, ld_slot(t.slots + gq.bin));
+    if (nr == 0) return c.foreign ? ST_CONFLICT : ST_FAILED;
+    for (uint32_t i = 0; i < nr; i++) {
+      const uint32_t g = rg[i], y = ry[i];
+      View<1> vy;
+      load_view<1>(t, y, vy);
+      if (claimed_mask<1>(vy)) c.foreign = 1;
+      if (!free_mask<1>(vy)) {
+        push(y, vy.m, g << 3);
+        continue;
+      }
+      // path: root group -> ... -> group g, one record each, in chain order
+      uint32_t depth = 1;
+      for (uint32_t q = g; G[q].parent != ~0u; q = G[q].parent >> 3) depth++;
+      if ((int)depth + 4 > c.pcap) return ST_LONG;
+      {
+        uint32_t q = g;
+        for (int e = (int)depth - 1; e >= 0; e--) {
+          set_entry(c, e, pack_entry(G[q].bin, 0, K_MOVE, false, 0, 0), q);
+          if (G[q].parent != ~0u) q = G[q].parent >> 3;
+        }
+      }
+      // claim the path in chain order from the metadata words as viewed; the
+      // record read after a claim is the one the search saw
+      c.pn = 0;
+      for (uint32_t e = 0; e < depth; e++) {
+        Group gq = G[(uint32_t)content_at(c, (int)e)];
+        if (gq.stale) return ST_CONFLICT;
+        if (!cas_acquire(t.meta + gq.bin, gq.meta, gq.meta + 1u)) return ST_CONFLICT;
+        c.pn = (int)e + 1;
+        set_content(c, (int)e, ld_slot(t.slots + gq.bin));
+      }
+      c.kicks = depth;
+      return take_free<1>(t, c, y, vy, 0, false);
     }
-    c.kicks = depth;
-    return take_free<1>(t, c, y, vy, 0, false);
+    if (out) return c.foreign ? ST_CONFLICT : ST_FAILED;
   }
 }
 

@@ -14,7 +14,10 @@ pytestmark = pytest.mark.gpu
 
 
 def small_workload(n_tables=64, seed=7):
-    bins, slots = inputs.multi_shapes(n_tables, seed=seed, lo_log2=8, hi_log2=12)
+    # tables of 2^10 .. 2^13 bins: with a tile of keys per block, at most a
+    # few percent of a table's slots are in flight, the regime the claim
+    # protocol is built for (the benchmark's tables keep far fewer)
+    bins, slots = inputs.multi_shapes(n_tables, seed=seed, lo_log2=10, hi_log2=13)
     keys, vals, n_keys = inputs.multi_keys(bins, slots, 0.95)
     return bins, slots, keys, vals, n_keys
 
@@ -27,12 +30,15 @@ def test_batched_equals_per_table_and_oracle(policy, tile):
     a = M.MultiTable(bins, slots, n_keys, policy, seed=5)
     b = M.MultiTable(bins, slots, n_keys, policy, seed=5)
     a.set_param(M.MULTI_TILE, tile)
+    a.set_param(M.MULTI_BLOCK, 128)
+    b.set_param(M.MULTI_BLOCK, 128)
     sa = torch.empty(len(keys), dtype=torch.uint8, device="cuda")
     sb = torch.empty(len(keys), dtype=torch.uint8, device="cuda")
     a.insert(kt, vt, sa)
     b.insert(kt, vt, sb, per_table=True)
     torch.cuda.synchronize()
-    assert bool((sa == 0).all()) and bool((sb == 0).all())
+    assert bool((sa == 0).all()), np.bincount(sa.cpu().numpy())
+    assert bool((sb == 0).all()), np.bincount(sb.cpu().numpy())
     off = 0
     for i in range(len(bins)):
         n = int(n_keys[i])

@@ -113,6 +113,30 @@ def test_serial_replay_matches_oracle_exactly(bins, B, d, policy, load):
     check_table(slots, meta, bins, B, d, family)
 
 
+SPAWN_K_CASES = [(1 << 14, 4, 2, ck.BFS, 0.95), (1 << 14, 4, 2, ck.SORTED | ck.GHOST, 0.97),
+                 (1 << 12, 8, 2, ck.HYBRID, 0.97), (1 << 14, 1, 4, ck.SORTED, 0.95)]
+
+
+@pytest.mark.parametrize("bins,B,d,policy,load", SPAWN_K_CASES,
+                         ids=["%dx%d-d%d-%s-%.2f" % (b, s, d, pname(p), l) for b, s, d, p, l in SPAWN_K_CASES])
+def test_serial_replay_in_rounds_matches_oracle(bins, B, d, policy, load):
+    """Searches spawning 4 records a round (Sec. 5 prefetching): layout,
+    statuses and bins viewed equal the oracle's."""
+    keys, vals, _ = fill_case(bins, B, d, load, 1)
+    ref, t, family = make_pair(bins, B, d, policy, 7, 500)
+    ref.set_spawn_k(4)
+    t.set_param(ck.PARAM_SPAWN_K, 4)
+    ost, oviewed, _ = ref.insert(keys, vals, trace=True)
+    viewed = torch.zeros(len(keys), dtype=torch.int32, device="cuda")
+    st = t.insert(ck.as_u32_tensor(keys), ck.as_u32_tensor(vals), viewed=viewed, serial=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(st.cpu().numpy(), ost)
+    assert np.array_equal(ck.u32_numpy(viewed), oviewed)
+    slots, meta = t.export()
+    assert np.array_equal(slots, ref.export()["rec"])
+    check_table(slots, meta, bins, B, d, family)
+
+
 CONCURRENT_CASES = (
     [(1 << 16, 4, 2, p, 0.95) for p in TWO_CHOICE]
     + [(1 << 15, 8, 2, p, 0.97) for p in (ck.RANDOM, ck.QUEUE, ck.SORTED | ck.GHOST)]

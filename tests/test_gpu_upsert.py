@@ -1,0 +1,53 @@
+"""Upsert (CK_INS_UPSERT, the absent-key assumption of Sec. 3 lifted)
+against the oracle: a present key gets its value overwritten in every copy
+(status CK_ST_UPDATED), an absent key is inserted.  Serial replay equals
+the oracle slot for slot; concurrent batches give the same statuses and the
+same key->value map."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1605_05236_gb300 import ck, inputs
+from table_checks import check_table
+
+pytestmark = pytest.mark.gpu
+
+CASES = [(1 << 12, 4, 2, ck.QUEUE), (1 << 12, 4, 2, ck.SORTED | ck.GHOST), (1 << 11, 8, 2, ck.RANDOM | ck.GHOST),
+         (1 << 14, 1, 3, ck.RATTLE), (1 << 14, 1, 4, ck.HYBRID)]
+
+
+def workload(bins, B, seed):
+    pre, nxt = inputs.distinct_keys(inputs.load_target(bins * B, 0.75), seed)
+    fresh, _ = inputs.distinct_keys(inputs.load_target(bins * B, 0.15), seed, exclude=pre, start=nxt)
+    # half present keys (new values), half absent keys, shuffled
+    present = pre[inputs.permutation(len(pre), seed + 1, len(fresh))]
+    ks = np.concatenate([present, fresh])[inputs.permutation(2 * len(fresh), seed + 2)]
+    vs = (inputs.values_for(ks) ^ np.uint32(0x5A5A5A5A)).astype(np.uint32)
+    return pre, ks, vs
+
+
+@pytest.mark.parametrize("bins,B,d,policy", CASES, ids=lambda x: str(x))
+@pytest.mark.parametrize("serial", [True, False])
+def test_upsert_matches_oracle(bins, B, d, policy, serial):
+    pre, ks, vs = workload(bins, B, 21)
+    ref = oracle.OracleTable(bins, B, d, policy, rng_seed=5, cap=500)
+    t = ck.CuckooTable(bins, B, d, policy, seed=5)
+    assert (ref.insert(pre, inputs.values_for(pre)) == 0).all()
+    t.insert(ck.as_u32_tensor(pre), ck.as_u32_tensor(inputs.values_for(pre)), serial=True)
+    torch.cuda.synchronize()
+    assert t.contents() == ref.contents()
+    ost = ref.upsert(ks, vs)
+    st = t.insert(ck.as_u32_tensor(ks), ck.as_u32_tensor(vs), serial=serial, upsert=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(st.cpu().numpy(), ost)
+    assert (ost == ck.ST_UPDATED).sum() == len(ks) // 2
+    assert t.contents() == ref.contents()
+    s = t.stats()
+    assert s["updates"] == len(ks) // 2 and s["size"] == len(pre) + len(ks) // 2
+    slots, meta = t.export()
+    if serial:
+        assert np.array_equal(slots, ref.export()["rec"])
+    check_table(slots, meta, bins, B, d)
+    v, f = t.lookup(ck.as_u32_tensor(ks))
+    assert bool((f == 1).all()) and np.array_equal(ck.u32_numpy(v), vs)

@@ -29,7 +29,7 @@ def parse(path):
             for p in kv["policy"].split("|"):
                 pol |= POLICIES[p]
             table = dict(bins=int(kv["bins"]), B=int(kv["B"]), d=int(kv["d"]), policy=pol,
-                         cap=int(kv["cap"]))
+                         cap=int(kv["cap"]), spawn_k=int(kv.get("spawn_k", 1)))
         elif head == "insert":
             lhs, rhs = rest.split("->")
             kv = dict(x.split("=") for x in lhs.split())
@@ -59,6 +59,7 @@ def test_golden(path):
                            cap=table["cap"])
     keys = sorted(keybins)
     t.set_bins(np.array(keys, dtype=np.uint32), np.array([keybins[k] for k in keys], dtype=np.uint64))
+    t.set_spawn_k(table["spawn_k"])
     for step in steps:
         if step[0] == "insert":
             _, key, val, st, viewed, kicks = step

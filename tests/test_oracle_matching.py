@@ -68,6 +68,20 @@ def test_walks_never_overfill(policy, B):
     assert ok > 0 and fail > 0
 
 
+@pytest.mark.parametrize("policy", [oracle.BFS, oracle.SORTED | oracle.GHOST, oracle.HYBRID])
+def test_search_in_rounds_is_complete(policy, monkeypatch):
+    # spawning k records a round (Sec. 5) changes the order and the views,
+    # not which bins an unbounded search reaches
+    orig = oracle.OracleTable.__init__
+
+    def init(self, *a, **kw):
+        orig(self, *a, **kw)
+        self.set_spawn_k(4)
+    monkeypatch.setattr(oracle.OracleTable, "__init__", init)
+    ok, fail = run_trials(2, 2, policy, 40, 500 + policy, complete=True)
+    assert ok > 0 and fail > 0
+
+
 @pytest.mark.parametrize("d,policy", [(3, oracle.BFS), (4, oracle.BFS), (3, oracle.SORTED), (4, oracle.SORTED),
                                       (3, oracle.HYBRID), (4, oracle.HYBRID)])
 def test_dary_search_is_complete(d, policy):

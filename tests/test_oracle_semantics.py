@@ -146,3 +146,34 @@ def test_reserved_key_rejected():
     st = t.insert([0xFFFFFFFF, 5], [1, 2])
     assert list(st) == [oracle.ST_INVALID, oracle.ST_OK]
     assert t.contents() == {5: 2}
+
+
+@pytest.mark.parametrize("d,B,policy", [(2, 4, oracle.QUEUE), (2, 4, oracle.SORTED | oracle.GHOST),
+                                        (2, 8, oracle.RANDOM | oracle.GHOST), (3, 1, oracle.RATTLE),
+                                        (4, 1, oracle.HYBRID)])
+def test_upsert_against_a_dict(d, B, policy):
+    """Upsert lifts the absent-key assumption of Sec. 3: present keys get the
+    new value (every copy of a ghost pair), absent keys are inserted."""
+    bins = 256 if B > 1 else 1024
+    t = oracle.OracleTable(bins, B, d, policy, rng_seed=3, cap=500)
+    rng = np.random.default_rng(7)
+    pool, _ = inputs.distinct_keys(int(bins * B * 0.8), 61)
+    want = {}
+    for rnd in range(6):
+        ks = rng.choice(pool, 300, replace=False).astype(np.uint32)
+        vs = rng.integers(0, 2**32 - 1, len(ks), dtype=np.uint64).astype(np.uint32)
+        present = np.array([int(k) in want for k in ks])
+        st = t.upsert(ks, vs)
+        assert (st[present] == oracle.ST_UPDATED).all()
+        assert (st[~present] == oracle.ST_OK).all()
+        for k, v in zip(ks, vs):
+            want[int(k)] = int(v)
+        assert t.contents() == want
+        assert t.check_invariants()[0] == 0
+    s = t.stats()
+    assert s["size"] == len(want)
+    e = t.export()
+    if policy & oracle.GHOST:  # both copies of a ghost pair carry the new value
+        recs = e["rec"][e["dup"] == 1]
+        for r in recs:
+            assert (int(r) & 0xFFFFFFFF) == want[int(r) >> 32]
