@@ -422,14 +422,6 @@ static int lowest_dup(const orc_table *t, uint64_t bin) {
 }
 
 /* first slot from `start` onwards (cyclically) satisfying the predicate */
-static int first_free_from(const orc_table *t, uint64_t bin, uint32_t start) {
-  for (uint32_t i = 0; i < t->B; i++) {
-    uint32_t s = (start + i) % t->B;
-    if (is_free(t, bin * t->B + s)) return (int)s;
-  }
-  return -1;
-}
-
 static int first_dup_from(const orc_table *t, uint64_t bin, uint32_t start) {
   for (uint32_t i = 0; i < t->B; i++) {
     uint32_t s = (start + i) % t->B;
@@ -554,8 +546,9 @@ static int insert_random2(orc_table *t, uint64_t krec, const uint64_t *b) {
 /* Each insertion into a bin takes the bin's hit counter h and increments
  * it; the record goes to slot h mod B, kicking out its occupant (the record
  * that has been in the bin longest).  Readings: when the bin still has a
- * free slot the first free slot from h mod B is used (in insert-only tables
- * this is slot h mod B itself); with ghosts a duplicate, searched from
+ * free slot the record takes the lowest free slot (in insert-only tables
+ * the bin fills in slot order, so this is slot h mod B itself; after
+ * deletes a free slot wins over kicking); with ghosts a duplicate, searched from
  * h mod B, is overwritten before any plain record is kicked; a slot the
  * chain already wrote is skipped.  The new key views both bins and takes
  * the less full one (load balancing, Sec. 2), b0 on ties; when both are
@@ -566,10 +559,10 @@ static int insert_queue(orc_table *t, uint64_t krec, const uint64_t *b) {
   view(t); view(t);
   int f0 = count_free(t, b0), f1 = count_free(t, b1);
   if (t->ghost && f0 > 0 && f1 > 0) {
-    uint32_t h0 = hit_take(t, b0);
-    int s0 = first_free_from(t, b0, h0 % t->B);
-    uint32_t h1 = hit_take(t, b1);
-    int s1 = first_free_from(t, b1, h1 % t->B);
+    hit_take(t, b0);
+    int s0 = lowest_free(t, b0);
+    hit_take(t, b1);
+    int s1 = lowest_free(t, b1);
     put_ghost_pair(t, b0, s0, b1, s1, krec);
     return ORC_OK;
   }
@@ -580,7 +573,7 @@ static int insert_queue(orc_table *t, uint64_t krec, const uint64_t *b) {
   uint64_t cur = krec;
   for (;;) {
     uint32_t h = hit_take(t, x) % t->B;
-    int s = first_free_from(t, x, h);
+    int s = lowest_free(t, x);
     if (s >= 0) { prop41_check(t, x); put(t, x * t->B + s, cur, 0, 0); return ORC_OK; }
     if (t->ghost && (s = first_dup_from(t, x, h)) >= 0) { prop41_check(t, x); evict_dup(t, x, s, cur); return ORC_OK; }
     s = first_unclaimed_from(t, x, h);

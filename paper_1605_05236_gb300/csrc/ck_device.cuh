@@ -340,6 +340,15 @@ __device__ __forceinline__ uint32_t free_mask(const View<B>& v) {
   return m & ~claimed_mask(v);
 }
 
+// Empty slots whatever their claim bits (a view that read no metadata word).
+template <int B>
+__device__ __forceinline__ uint32_t empty_mask(const View<B>& v) {
+  uint32_t m = 0;
+#pragma unroll
+  for (int s = 0; s < B; s++) m |= (v.s[s] == EMPTY ? 1u : 0u) << s;
+  return m;
+}
+
 template <int B>
 __device__ __forceinline__ uint32_t dup_mask(const View<B>& v) {
   uint32_t m = 0;

@@ -407,9 +407,12 @@ __device__ int insert_random2(const DevTable& t, Ctx& c) {
 // ------------------------------------------------------------------
 // queue-kicking with hit counters and hit balancing (Sec. 6)
 // ------------------------------------------------------------------
-// The claim of a slot and the increment of the bin's hit counter are one
-// compare-and-swap, the GPU form of the paper's fetch-and-add scheduling:
-// B insertions arriving at one bin are handed B different slots.
+// Every placement into a bin takes its hit counter h and increments it (the
+// claim of a kicked slot and the increment are one compare-and-swap, the GPU
+// form of the paper's fetch-and-add scheduling).  A record goes to the
+// lowest free slot (in insert-only tables the bin fills in slot order, so
+// this is slot h mod B); a full bin gives up its first unclaimed slot from
+// h mod B, the record that has been there longest.
 template <int B, bool GHOST>
 __device__ int insert_queue(const DevTable& t, Ctx& c) {
   constexpr uint32_t FULL = (1u << B) - 1;
@@ -417,19 +420,24 @@ __device__ int insert_queue(const DevTable& t, Ctx& c) {
   bins2(t, c.key, b0, b1);
   View<B> v0, v1;
   if (!GHOST) {
-    // the common case first: a free slot in the less full bin, placed by a
-    // compare-and-swap of the slot on an unordered view
-    load_view_fast<B>(t, b0, v0);
-    load_view_fast<B>(t, b1, v1);
+    // the common case first: the lowest empty slot of the less full bin,
+    // taken by a compare-and-swap of the slot; only the two bins' slots are
+    // read (an empty slot another insertion claimed as its chain's end is
+    // taken all the same: that chain finds it gone when it commits)
+    load_slots<B>(t, b0, v0);
+    load_slots<B>(t, b1, v1);
     c.viewed += 2;
-    uint32_t g0 = free_mask<B>(v0), g1 = free_mask<B>(v1);
+    uint32_t g0 = empty_mask<B>(v0), g1 = empty_mask<B>(v1);
     if (g0 | g1) {
       bool first = __popc(g0) >= __popc(g1);
       uint32_t x = first ? b0 : b1;
-      int s = first_from<B>(first ? g0 : g1, hit_of(first ? v0.m : v1.m) % B);
+      int s = lowest(first ? g0 : g1);
       return place_direct<B>(t, c, x, s, true) ? (int)ST_OK : (int)ST_CONFLICT;
     }
-    fence_acquire();  // both metadata words before both bins' slots
+    // both full: the metadata words, then the slots again after them
+    v0.m = ld_relaxed(t.meta + b0);
+    v1.m = ld_relaxed(t.meta + b1);
+    fence_acquire();
     load_slots<B>(t, b0, v0);
     load_slots<B>(t, b1, v1);
   } else {
@@ -439,8 +447,8 @@ __device__ int insert_queue(const DevTable& t, Ctx& c) {
   uint32_t fm0 = free_mask<B>(v0), fm1 = free_mask<B>(v1);
   int f0 = __popc(fm0), f1 = __popc(fm1);
   if (GHOST && f0 > 0 && f1 > 0) {
-    int s0 = first_from<B>(fm0, hit_of(v0.m) % B);
-    int s1 = first_from<B>(fm1, hit_of(v1.m) % B);
+    int s0 = lowest(fm0);
+    int s1 = lowest(fm1);
     if (!claim(t, c, b0, v0.m, s0, K_GHOST, true, EMPTY)) return ST_CONFLICT;
     if (!claim(t, c, b1, v1.m, s1, K_GHOST, true, EMPTY)) return ST_CONFLICT;
     c.ghosts_made++;
@@ -467,7 +475,7 @@ __device__ int insert_queue(const DevTable& t, Ctx& c) {
       uint32_t h = hit_of(vx.m) % B;
       uint32_t fm = free_mask<B>(vx);
       if (fm) {
-        if (claim(t, c, x, vx.m, first_from<B>(fm, h), K_MOVE, true, EMPTY)) return ST_OK;
+        if (claim(t, c, x, vx.m, lowest(fm), K_MOVE, true, EMPTY)) return ST_OK;
       } else if (GHOST && dup_mask<B>(vx)) {
         return take_dup<B>(t, c, x, vx, first_from<B>(dup_mask<B>(vx), h), true);
       } else {
