@@ -233,3 +233,76 @@ def serving_trace(prefill_keys: np.ndarray, n_req: int, mix: tuple, seed: int = 
         pos[o] += n
     return {"op": op, "n_keys": n_keys, "key_off": key_off, "arrive_ns": arrive, "keys": keys,
             "vals": values_for(keys), "expect": expect}
+
+
+TX_INSERT, TX_READ, TX_OVERWRITE, TX_DELETE = 0, 1, 2, 3
+
+
+def txn_workload(n_workers: int, txns_per_worker: int, ops_per_txn: int, mix: tuple, seed: int = 13):
+    """Transactions for the transactional layer (Sec. 8 experiments).
+
+    Worker w runs transactions w*T .. w*T + T - 1 in order, each of
+    `ops_per_txn` operations: insert / delete / overwrite / read with
+    weights `mix` (the paper's delete-light 1:0:1:1 and delete-heavy
+    2:1:2:2).  Inserts take fresh distinct keys (stream of `seed`) and
+    random values; a read, overwrite or delete picks one of the worker's
+    own keys inserted by an earlier transaction and not deleted (the
+    paper: "out of all records ever inserted into the table by the
+    thread"), at most once per transaction; with none available the op is
+    an insert.  Choices come from SplitMix64 streams of seed+1 (kinds),
+    seed+2 (targets) and seed+3 (values).  Returns dict(op, key, val) of
+    n_workers * T * ops_per_txn entries, transaction-major."""
+    n = n_workers * txns_per_worker * ops_per_txn
+    fresh, _ = distinct_keys(n, seed)
+    kind_u = (splitmix64_stream(seed + 1, 0, n) >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+    pick = splitmix64_stream(seed + 2, 0, n)
+    vals = (splitmix64_stream(seed + 3, 0, n) >> np.uint64(32)).astype(np.uint32)
+    cum = np.cumsum(mix) / float(np.sum(mix))
+    kinds = np.minimum(np.searchsorted(cum, kind_u, side="right"), 3)
+    # mix order is (insert, delete, overwrite, read)
+    code = np.array([TX_INSERT, TX_DELETE, TX_OVERWRITE, TX_READ], dtype=np.uint8)[kinds]
+    op = np.empty(n, dtype=np.uint8)
+    key = np.empty(n, dtype=np.uint32)
+    nxt = 0
+    for w in range(n_workers):
+        live = []          # keys of this worker present after its committed transactions
+        pos = {}           # key -> index in live
+        for t in range(txns_per_worker):
+            base = (w * txns_per_worker + t) * ops_per_txn
+            used = set()
+            born, dead = [], []
+            for j in range(ops_per_txn):
+                i = base + j
+                c = int(code[i])
+                if c != TX_INSERT:
+                    cand = None
+                    if len(live) > len(used):
+                        for probe in range(8):
+                            k = live[int((pick[i] >> np.uint64(8 * probe)) % np.uint64(len(live)))]
+                            if k not in used:
+                                cand = k
+                                break
+                    if cand is None:
+                        c = TX_INSERT
+                if c == TX_INSERT:
+                    k = int(fresh[nxt])
+                    nxt += 1
+                    born.append(k)
+                else:
+                    k = cand
+                    if c == TX_DELETE:
+                        dead.append(k)
+                used.add(k)
+                op[i] = c
+                key[i] = k
+            for k in dead:  # the transaction's effects, for the next ones
+                last = live.pop()
+                if last != k:
+                    live[pos[k]] = last
+                    pos[last] = pos[k]
+                del pos[k]
+            for k in born:
+                pos[k] = len(live)
+                live.append(k)
+    return {"op": op, "key": key, "val": vals, "workers": n_workers, "txns_per_worker": txns_per_worker,
+            "ops_per_txn": ops_per_txn}
