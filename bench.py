@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-multi", action="store_true", help="skip the batched form (4096 tables)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving form")
-    ap.add_argument("--only", choices=["serve", "multi", "policies"],
+    ap.add_argument("--no-txn", action="store_true", help="skip the transactional layer's abort counts")
+    ap.add_argument("--only", choices=["serve", "multi", "policies", "txn"],
                     help="run one side section alone and print its JSON (diagnostics; no bench line)")
     return ap.parse_args()
 
@@ -490,6 +491,79 @@ def serve_form(torch, ck, stream):
     return out
 
 
+TXN_BINS, TXN_B, TXN_WORKERS, TXN_OPS, TXN_TRIALS = 1 << 14, 8, 15, 100, 100
+TXN_DENSITIES = (0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 0.95)
+TXN_MIXES = (("delete_light", (1, 0, 1, 1)), ("delete_heavy", (2, 1, 2, 2)))
+
+
+def txn_form(torch, stream):
+    """The transactional layer (Sec. 8) on the paper's experiment: tables
+    of 2^14 bins x 8 slots, 15 workers each running 100-operation
+    transactions (insert:delete:overwrite:read 1:0:1:1 and 2:1:2:2; targets
+    drawn among the worker's own earlier inserts, deleted ones included)
+    until the table holds 95% of its slots; 100 trials (independent tables,
+    salted hash seeds) side by side in one launch per implementation.  For
+    each of the six implementations: the mean number of aborts over a
+    table's lifetime up to each density (the figures' curves), the share of
+    attempts that aborted, abort causes, and the committed transactions per
+    second of the whole launch."""
+    import numpy as np
+    from paper_1605_05236_gb300 import inputs, txn
+    cap = TXN_BINS * TXN_B
+    fill_to = int(0.95 * cap)
+    res = {"table": "2^14 x 8 slots per trial", "workers": TXN_WORKERS, "ops_per_txn": TXN_OPS,
+           "trials": TXN_TRIALS, "densities": list(TXN_DENSITIES)}
+    for mix_name, mix in TXN_MIXES:
+        t_max = 4 * fill_to * sum(mix) // (TXN_WORKERS * TXN_OPS * max(1, mix[0] - mix[1])) + 10
+        work = inputs.txn_workload(TXN_WORKERS, t_max, TXN_OPS, mix, seed=13, fill_to=fill_to)
+        T = work["txns_per_worker"]
+        n = len(work["op"])
+        op = torch.from_numpy(work["op"]).cuda()
+        key = torch.from_numpy(work["key"].view(np.int32)).cuda()
+        val = torch.from_numpy(work["val"].view(np.int32)).cuda()
+        section = {"mix": ":".join(map(str, mix)), "txns_per_worker": T, "ops": n}
+        for name, flags in txn.VARIANTS:
+            tab = txn.TxnTable(TXN_BINS, TXN_B, TXN_TRIALS, seed=21)
+            start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            start.record(stream)
+            out = tab.run(op, key, val, TXN_WORKERS, T, TXN_OPS, flags, want_values=False, stream=stream)
+            end.record(stream)
+            end.synchronize()
+            ms = start.elapsed_time(end)
+            s = tab.stats()
+            st = out["status"].cpu().numpy().reshape(TXN_TRIALS, n)
+            att = out["attempts"].cpu().numpy().reshape(TXN_TRIALS, -1)
+            order = out["order"].cpu().numpy().reshape(TXN_TRIALS, -1)
+            ab = np.zeros((TXN_TRIALS, len(TXN_DENSITIES)), dtype=np.float64)
+            at = np.zeros_like(ab)
+            for r in range(TXN_TRIALS):
+                a, t_ = txn.aborts_by_density(st[r], work["op"], att[r], order[r], TXN_OPS, cap, TXN_DENSITIES)
+                ab[r], at[r] = a, t_
+            reached = (ab >= 0).all(0)
+            section[name] = {
+                "mean_aborts_by_density": [round(float(ab[:, j].mean()), 2) if reached[j] else None
+                                           for j in range(len(TXN_DENSITIES))],
+                "abort_pct_by_density": [round(100.0 * float(ab[:, j].sum() / at[:, j].sum()), 4) if reached[j]
+                                         else None for j in range(len(TXN_DENSITIES))],
+                "abort_pct": round(100.0 * (s["attempts"] - s["commits"]) / max(1, s["attempts"]), 4),
+                "statuses_same_in_every_trial": bool((st == st[0]).all()),
+                "causes": {k: s[k] for k in ("abort_claimed", "abort_lock", "abort_ws", "abort_rs", "abort_chain",
+                                             "abort_overflow")},
+                "failed": s["failed"], "local_retries": s["local_retries"], "mini_txns": s["mini_txns"],
+                "kicks_per_insert": round(s["kicks"] / max(1, int((work["op"] == txn.TX_INSERT).sum()) * TXN_TRIALS), 4),
+                "ms": round(ms, 2),
+                "k_txns_per_s": round(s["commits"] / ms, 1),
+            }
+            tab.close()
+        naive, best = section["naive"]["mean_aborts_by_density"], section["claim_system"]["mean_aborts_by_density"]
+        section["naive_over_claim_system"] = [round(a / b, 1) if a is not None and b else None
+                                              for a, b in zip(naive, best)]
+        res[mix_name] = section
+        del op, key, val
+    return res
+
+
 def cpu_baseline():
     """The oracle, as it stands, on one host core: a bounded sample of the
     workload (a 2^22-bin x 4-slot table filled to 0.95 with queue-kicking)."""
@@ -660,6 +734,8 @@ def run_gpu(args, rank, world, local):
         out["batched_form"] = multi_form(torch, ck, stream)
     if rank == 0 and world == 1 and not args.no_serve:
         out["serving_form"] = serve_form(torch, ck, stream)
+    if rank == 0 and world == 1 and not args.no_txn:
+        out["transactional"] = txn_form(torch, stream)
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline()
     if world > 1:
@@ -804,6 +880,8 @@ def run_section(name):
         return {"serving_form": serve_form(torch, ck, stream)}
     if name == "multi":
         return {"batched_form": multi_form(torch, ck, stream)}
+    if name == "txn":
+        return {"transactional": txn_form(torch, stream)}
     keys, vals, _, _, _ = workload(rank_seed(0))
     return {"policies": policy_fills(torch, ck, stream, (keys, vals))}
 

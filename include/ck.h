@@ -370,6 +370,97 @@ int ck_server_info(ck_server *s, uint64_t *waves, uint64_t *busy_rejects, double
 /* Stop the threads (after draining) and free the server (not the table). */
 void ck_server_destroy(ck_server *s);
 
+/* ---- transactional layer (Sec. 8) ----
+ *
+ * Transactions of inserts, reads, overwrites and deletes on two-choice
+ * tables of n bins x B slots, under the optimistic concurrency scheme of
+ * Sec. 8 (read and write sets of version IDs; Stage 1 plans, Stage 2 locks
+ * the write set in a global order and verifies both sets, Stage 3 applies
+ * and stamps every written slot and bin with the transaction ID), with the
+ * mechanisms of Sec. 8 that reduce aborts as flags.
+ *
+ * One handle holds `trials` independent tables, run side by side by one
+ * launch: trial r hashes with its own salted seed pair, and all trials run
+ * the same operation arrays.  A worker (the paper's thread) is one warp and
+ * runs its transactions in order; workers run concurrently.  Every wait on a
+ * lock is bounded; a lock not obtained within the bound aborts the attempt,
+ * and an aborted attempt runs again: at most 100,000 attempts, and none
+ * once the worker has run 120 s in this launch (its remaining transactions
+ * are given up).
+ *
+ * Operations (d_op): CK_TX_INSERT (key, val): adds the record; status 0,
+ * or 1 if the key was present already (nothing written).  CK_TX_READ: status
+ * 1 and the value if present, else status 0.  CK_TX_OVERWRITE /
+ * CK_TX_DELETE: status 1 if the key was present (value replaced / record
+ * removed), else 0.  A transaction names each key at most once.  A
+ * transaction given up (attempt or time bound, or an insert with no
+ * placement within 500 kick-outs) gets status 255 on all its operations and
+ * writes nothing. */
+#define CK_TX_INSERT 0
+#define CK_TX_READ 1
+#define CK_TX_OVERWRITE 2
+#define CK_TX_DELETE 3
+
+/* Mechanisms (Sec. 8 "Mechanisms for Reducing Aborts"; queue-kicking with
+ * hit counters, Sec. 5).  No flag: the naive scheme (random kicking). */
+#define CK_TXF_LOCAL_RETRY 1u  /* a moved bin version: re-check the key's absence, not abort */
+#define CK_TXF_QUEUE 2u        /* the slot a record takes is the bin's hit counter mod B */
+#define CK_TXF_SYSTEM 4u       /* kick-out chains done in Stage 1, last move first, one small transaction each */
+#define CK_TXF_CLAIM 8u        /* slots joining a write set are claimed; chains pass over claimed slots */
+
+#define CK_TXN_MAX_OPS 256     /* operations per transaction */
+#define CK_TXN_COUNTERS 16
+/* counters of ck_txn_stats, summed over trials since the last create/reset */
+#define CK_TXS_COMMITS 0
+#define CK_TXS_ATTEMPTS 1
+#define CK_TXS_ABORT_CLAIMED 2   /* an overwrite/delete or a planned slot met another's claim */
+#define CK_TXS_ABORT_LOCK 3      /* a lock not obtained within the bound */
+#define CK_TXS_ABORT_WS 4        /* a write-set version moved */
+#define CK_TXS_ABORT_RS 5        /* a read-set version moved / a key appeared */
+#define CK_TXS_ABORT_CHAIN 6     /* no eligible slot for an insert or chain step */
+#define CK_TXS_ABORT_OVERFLOW 7  /* read set (512) or write set (512) full */
+#define CK_TXS_LOCAL_RETRIES 8
+#define CK_TXS_FAILED 9
+#define CK_TXS_MINI_TXNS 10      /* chain moves done as small transactions (CK_TXF_SYSTEM) */
+#define CK_TXS_MINI_ABORTS 11
+#define CK_TXS_KICKS 12
+
+typedef struct ck_txn_table ck_txn_table;
+
+/* `trials` empty tables of `bins` bins x `slots_per_bin` (4 or 8) slots
+ * each; trials * bins * slots_per_bin < 2^31.  Device memory: 16 bytes per
+ * slot and 12 per bin, plus 57,344 bytes of transaction scratch per worker
+ * at the first ck_txn_run.  Synchronous. */
+int ck_txn_create(ck_txn_table **out, uint64_t bins, uint32_t slots_per_bin, uint32_t trials, uint64_t seed);
+
+/* Empty every trial's table and zero the counters.  Synchronous. */
+int ck_txn_reset(ck_txn_table *x);
+
+/* Run n_workers workers on every trial: worker w runs transactions
+ * w*T .. w*T + T - 1 (T = txns_per_worker) in order; transaction i is
+ * operations i*L .. i*L + L - 1 (L = ops_per_txn <= CK_TXN_MAX_OPS) of the
+ * device arrays d_op, d_key, d_val (n_workers*T*L entries, shared by all
+ * trials; keys != 0xFFFFFFFF).  Outputs, all device memory and each
+ * optional (NULL: not written): d_status, d_value per operation and trial
+ * (trials*n_workers*T*L, trial-major); per transaction and trial
+ * (trials*n_workers*T): d_attempts (attempts made), d_tid (the committed
+ * transaction ID; per worker strictly increasing) and d_order (its position
+ * among its trial's commits; all ~0 for a transaction given up).  Flags:
+ * CK_TXF_*.  Asynchronous on `stream`. */
+int ck_txn_run(ck_txn_table *x, uint32_t flags, const uint8_t *d_op, const uint32_t *d_key,
+               const uint32_t *d_val, uint32_t n_workers, uint32_t txns_per_worker, uint32_t ops_per_txn,
+               uint8_t *d_status, uint32_t *d_value, uint32_t *d_attempts, uint64_t *d_tid, uint64_t *d_order,
+               void *stream);
+
+/* The first n (<= CK_TXN_COUNTERS) counters into host memory.  Synchronous. */
+int ck_txn_stats(ck_txn_table *x, uint64_t *h_counters, uint32_t n);
+
+/* Trial `trial`'s slots (bins*slots_per_bin packed records) into host
+ * memory.  Synchronous. */
+int ck_txn_export(ck_txn_table *x, uint32_t trial, uint64_t *h_slots);
+
+void ck_txn_destroy(ck_txn_table *x);
+
 /* Measurement helper (not an operation of the paper): n_reads independent
  * random reads of `width` bytes (8, 32 or 64: one single-slot, 4-slot or
  * 8-slot bin) from a device buffer of `bytes` bytes (64-byte aligned), the

@@ -238,21 +238,30 @@ def serving_trace(prefill_keys: np.ndarray, n_req: int, mix: tuple, seed: int = 
 TX_INSERT, TX_READ, TX_OVERWRITE, TX_DELETE = 0, 1, 2, 3
 
 
-def txn_workload(n_workers: int, txns_per_worker: int, ops_per_txn: int, mix: tuple, seed: int = 13):
+def txn_workload(n_workers: int, txns_per_worker: int, ops_per_txn: int, mix: tuple, seed: int = 13,
+                 fill_to: int | None = None):
     """Transactions for the transactional layer (Sec. 8 experiments).
 
     Worker w runs transactions w*T .. w*T + T - 1 in order, each of
     `ops_per_txn` operations: insert / delete / overwrite / read with
     weights `mix` (the paper's delete-light 1:0:1:1 and delete-heavy
     2:1:2:2).  Inserts take fresh distinct keys (stream of `seed`) and
-    random values; a read, overwrite or delete picks one of the worker's
-    own keys inserted by an earlier transaction and not deleted (the
-    paper: "out of all records ever inserted into the table by the
-    thread"), at most once per transaction; with none available the op is
-    an insert.  Choices come from SplitMix64 streams of seed+1 (kinds),
-    seed+2 (targets) and seed+3 (values).  Returns dict(op, key, val) of
-    n_workers * T * ops_per_txn entries, transaction-major."""
-    n = n_workers * txns_per_worker * ops_per_txn
+    random values.  A read, overwrite or delete targets a uniformly drawn
+    key among all the keys the same worker inserted in its earlier
+    transactions, deleted ones included (Sec. 8 draws from every record the
+    thread ever inserted), at most once per transaction; with none
+    available the operation becomes an insert.  Choices come from SplitMix64
+    streams of seed+1 (kinds), seed+2 (targets) and seed+3 (values).
+
+    `delta` is each transaction's net change of the table's size (inserts
+    less deletes of keys still present), from the generator's own record of
+    each worker's live keys.  With `fill_to`, every worker keeps only its
+    first t transactions, t the least for which the workers' total net
+    inserts reach `fill_to` (txns_per_worker is then an upper bound).
+    Returns dict(op, key, val, delta, workers, txns_per_worker,
+    ops_per_txn); operations transaction-major."""
+    T, L = txns_per_worker, ops_per_txn
+    n = n_workers * T * L
     fresh, _ = distinct_keys(n, seed)
     kind_u = (splitmix64_stream(seed + 1, 0, n) >> np.uint64(11)).astype(np.float64) / float(1 << 53)
     pick = splitmix64_stream(seed + 2, 0, n)
@@ -263,46 +272,53 @@ def txn_workload(n_workers: int, txns_per_worker: int, ops_per_txn: int, mix: tu
     code = np.array([TX_INSERT, TX_DELETE, TX_OVERWRITE, TX_READ], dtype=np.uint8)[kinds]
     op = np.empty(n, dtype=np.uint8)
     key = np.empty(n, dtype=np.uint32)
+    delta = np.zeros(n_workers * T, dtype=np.int64)
     nxt = 0
     for w in range(n_workers):
-        live = []          # keys of this worker present after its committed transactions
-        pos = {}           # key -> index in live
-        for t in range(txns_per_worker):
-            base = (w * txns_per_worker + t) * ops_per_txn
+        ever = []    # keys this worker inserted in earlier transactions
+        live = set()
+        for t in range(T):
+            base = (w * T + t) * L
             used = set()
-            born, dead = [], []
-            for j in range(ops_per_txn):
+            born = []
+            d = 0
+            for j in range(L):
                 i = base + j
                 c = int(code[i])
-                if c != TX_INSERT:
-                    cand = None
-                    if len(live) > len(used):
-                        for probe in range(8):
-                            k = live[int((pick[i] >> np.uint64(8 * probe)) % np.uint64(len(live)))]
-                            if k not in used:
-                                cand = k
-                                break
-                    if cand is None:
-                        c = TX_INSERT
+                cand = None
+                if c != TX_INSERT and ever:
+                    for probe in range(8):
+                        k = ever[int((pick[i] >> np.uint64(8 * probe)) % np.uint64(len(ever)))]
+                        if k not in used:
+                            cand = k
+                            break
+                if cand is None:
+                    c = TX_INSERT
                 if c == TX_INSERT:
                     k = int(fresh[nxt])
                     nxt += 1
                     born.append(k)
+                    d += 1
                 else:
                     k = cand
-                    if c == TX_DELETE:
-                        dead.append(k)
+                    if c == TX_DELETE and k in live:
+                        live.discard(k)
+                        d -= 1
                 used.add(k)
                 op[i] = c
                 key[i] = k
-            for k in dead:  # the transaction's effects, for the next ones
-                last = live.pop()
-                if last != k:
-                    live[pos[k]] = last
-                    pos[last] = pos[k]
-                del pos[k]
-            for k in born:
-                pos[k] = len(live)
-                live.append(k)
-    return {"op": op, "key": key, "val": vals, "workers": n_workers, "txns_per_worker": txns_per_worker,
-            "ops_per_txn": ops_per_txn}
+            ever.extend(born)
+            live.update(born)
+            delta[w * T + t] = d
+    if fill_to is not None:
+        per = delta.reshape(n_workers, T).cumsum(1).sum(0)  # total after t+1 transactions each
+        hit = np.nonzero(per >= fill_to)[0]
+        if not len(hit):
+            raise ValueError("txns_per_worker too small to reach fill_to")
+        t_keep = int(hit[0]) + 1
+        keep = (np.arange(n).reshape(n_workers, T, L)[:, :t_keep, :]).reshape(-1)
+        op, key, vals = op[keep], key[keep], vals[keep]
+        delta = delta.reshape(n_workers, T)[:, :t_keep].reshape(-1)
+        T = t_keep
+    return {"op": op, "key": key, "val": vals, "delta": delta, "workers": n_workers, "txns_per_worker": T,
+            "ops_per_txn": L}

@@ -58,3 +58,18 @@ def test_invalid_arguments_need_no_gpu():
     assert L.ck_stats(None, None) == ck.EINVAL
     assert ck.strerror(ck.EINVAL) == "invalid argument"
     assert ck.strerror(12345) == "unknown error"
+
+
+def test_txn_invalid_arguments_need_no_gpu():
+    from paper_1605_05236_gb300 import txn
+    L = txn._lib()
+    h = ctypes.c_void_p()
+    assert L.ck_txn_create(None, 1 << 10, 8, 1, 0) == ck.EINVAL
+    assert L.ck_txn_create(ctypes.byref(h), 1 << 10, 5, 1, 0) == ck.EINVAL   # B must be 4 or 8
+    assert L.ck_txn_create(ctypes.byref(h), 1 << 10, 8, 0, 0) == ck.EINVAL   # no trials
+    assert L.ck_txn_create(ctypes.byref(h), 1 << 28, 8, 1, 0) == ck.EINVAL   # slot indices overflow
+    assert L.ck_txn_run(None, 0, None, None, None, 1, 1, 1, None, None, None, None, None, None) == ck.EINVAL
+    assert L.ck_txn_reset(None) == ck.EINVAL
+    assert L.ck_txn_stats(None, None, 1) == ck.EINVAL
+    assert L.ck_txn_export(None, 0, None) == ck.EINVAL
+    L.ck_txn_destroy(None)

@@ -19,18 +19,18 @@ def test_replay_hand_worked():
     assert final == {1: 11, 8: 81}
 
 
-def test_workload_keeps_keys_per_worker_and_targets_live_keys():
+def test_workload_keeps_keys_per_worker_and_targets_earlier_keys():
     W, T, L = 5, 40, 20
     work = inputs.txn_workload(W, T, L, (2, 1, 2, 2), seed=3)
     op, key = work["op"], work["key"]
     owner = {}
     for w in range(W):
-        live = set()
+        ever = set()
         for t in range(T):
             base = (w * T + t) * L
             ks = key[base:base + L]
             assert len(set(ks.tolist())) == L  # a key at most once per transaction
-            dead, born = [], []
+            born = []
             for j in range(L):
                 k, o = int(ks[j]), int(op[base + j])
                 if o == I:
@@ -38,10 +38,31 @@ def test_workload_keeps_keys_per_worker_and_targets_live_keys():
                     owner[k] = w
                     born.append(k)
                 else:
-                    assert owner[k] == w and k in live  # own, live, earlier transaction
-                    if o == D:
-                        dead.append(k)
-            live -= set(dead)
-            live |= set(born)
-    st, _, _ = txn.replay(work)
-    assert (st[op != I] == 1).all()  # every read / overwrite / delete finds its key
+                    assert owner[k] == w and k in ever  # own, from an earlier transaction
+            ever |= set(born)
+    st, _, final = txn.replay(work)
+    # deleted keys stay targets: some operations miss, most find their key
+    miss = (st[op != I] == 0).mean()
+    assert 0.02 < miss < 0.6
+    # the generator's net inserts per transaction agree with the replay
+    sizes = np.zeros(W * T, dtype=np.int64)
+    for x in range(W * T):
+        sl = slice(x * L, (x + 1) * L)
+        sizes[x] = int((op[sl] == I).sum()) - int(((op[sl] == D) & (st[sl] == 1)).sum())
+    assert (sizes == work["delta"]).all()
+    assert int(work["delta"].sum()) == len(final)
+
+
+def test_workload_fill_to_keeps_a_prefix_of_each_worker():
+    W, T, L = 4, 60, 10
+    full = inputs.txn_workload(W, T, L, (1, 0, 1, 1), seed=5)
+    cut = inputs.txn_workload(W, T, L, (1, 0, 1, 1), seed=5, fill_to=300)
+    t = cut["txns_per_worker"]
+    assert t < T
+    per = full["delta"].reshape(W, T).cumsum(1).sum(0)
+    assert per[t - 1] >= 300 and (t == 1 or per[t - 2] < 300)
+    for w in range(W):
+        a = slice(w * t * L, (w + 1) * t * L)
+        b = slice(w * T * L, w * T * L + t * L)
+        assert (cut["op"][a] == full["op"][b]).all() and (cut["key"][a] == full["key"][b]).all()
+        assert (cut["val"][a] == full["val"][b]).all()
