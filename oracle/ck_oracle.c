@@ -145,7 +145,7 @@ typedef struct orc_table {
 /* ------------------------------------------------------------------ */
 
 /* MurmurHash3's 32-bit finalizer (Appleby, public domain): an invertible
- * avalanche mix used here as the "uniformly random hash" of Sec. 3. */
+ * avalanche mix standing in for Sec. 3's uniformly random hashes. */
 static uint32_t fmix32(uint32_t h) {
   h ^= h >> 16;
   h *= 0x85EBCA6Bu;
@@ -185,8 +185,8 @@ static int ov_find(const orc_table *t, uint32_t key) {
   return -1;
 }
 
-/* The d bins of a key (Sec. 1: "maps each key to two distinct bins";
- * Sec. 7 for d hash functions).  h_i = fmix32(key ^ seed_i) mod n (family
+/* The d bins of a key (Sec. 1: two different bins per key; Sec. 7 for d
+ * hash functions).  h_i = fmix32(key ^ seed_i) mod n (family
  * 0, the stated workload's hash), or, in family 1, a decorrelated form of
  * the same mix: fmix32(fmix32(key + seed_i) ^ (seed_i * 0x27D4EB2F)) mod n
  * (family 0's functions are not independent: key ^ seed_i ^ seed_j gets
@@ -598,12 +598,12 @@ static int insert_queue(orc_table *t, uint64_t krec, const uint64_t *b) {
  *
  * BFS pops the oldest candidate.  Sorted search pops the candidate with
  * the smallest spawn count; ties go to the oldest candidate, so equal
- * counts reduce to BFS.  Reading: a candidate's position in the sorted list
- * is fixed when it joins the list, by the spawn count its bin has at that
+ * counts reduce to BFS.  Reading: where a candidate sits in the priority
+ * order is fixed when it joins the list, by the spawn count its bin has at that
  * moment (the bucket sort of Sec. 5 keys each entry once).  Spawning a
  * record increments the spawn count of the bin holding it, saturating at 15
  * (four bits, Sec. 5); these increments persist even when the search fails
- * ("since the conception of the hash table").
+ * (the count covers the whole life of the table, Sec. 5).
  *
  * The sorted search / BFS hybrid (end of Sec. 5) orders candidates first by
  * the depth at which they were spawn victims (the records of b0 and b1:

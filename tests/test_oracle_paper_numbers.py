@@ -178,7 +178,7 @@ def test_curves_scale_with_table_size():
 
 @pytest.mark.slow
 def test_rattle_d3_needs_independent_hashes():
-    """Reading of Sec. 3 ("uniformly randomly generated hashes"): with the
+    """Reading of Sec. 3 (hashes taken as uniformly random): with the
     XOR-seeded family the d hash functions are not independent and 3-ary
     rattle-kicking at 90% fails keys in large tables; the decorrelated family
     behaves like independent hashes and fails (almost) none."""
