@@ -393,9 +393,12 @@ void ck_server_destroy(ck_server *s);
  * 1 and the value if present, else status 0.  CK_TX_OVERWRITE /
  * CK_TX_DELETE: status 1 if the key was present (value replaced / record
  * removed), else 0.  A transaction names each key at most once.  A
- * transaction given up (attempt or time bound, or an insert with no
- * placement within 500 kick-outs) gets status 255 on all its operations and
- * writes nothing. */
+ * transaction given up (attempt or time bound, an insert with no
+ * placement within 500 kick-outs, four attempts that overflowed the read
+ * set of 512 or the write set of 1024 entries, or 64 attempts whose inserts
+ * found no eligible slot) gets status 255 on all its operations and writes
+ * nothing.  Each operation takes up to 2 read-set
+ * entries; an insert takes 2 write-set entries plus 2 per kick-out. */
 #define CK_TX_INSERT 0
 #define CK_TX_READ 1
 #define CK_TX_OVERWRITE 2
@@ -418,7 +421,7 @@ void ck_server_destroy(ck_server *s);
 #define CK_TXS_ABORT_WS 4        /* a write-set version moved */
 #define CK_TXS_ABORT_RS 5        /* a read-set version moved / a key appeared */
 #define CK_TXS_ABORT_CHAIN 6     /* no eligible slot for an insert or chain step */
-#define CK_TXS_ABORT_OVERFLOW 7  /* read set (512) or write set (512) full */
+#define CK_TXS_ABORT_OVERFLOW 7  /* read set (512) or write set (1024) full */
 #define CK_TXS_LOCAL_RETRIES 8
 #define CK_TXS_FAILED 9
 #define CK_TXS_MINI_TXNS 10      /* chain moves done as small transactions (CK_TXF_SYSTEM) */
@@ -429,7 +432,7 @@ typedef struct ck_txn_table ck_txn_table;
 
 /* `trials` empty tables of `bins` bins x `slots_per_bin` (4 or 8) slots
  * each; trials * bins * slots_per_bin < 2^31.  Device memory: 16 bytes per
- * slot and 12 per bin, plus 57,344 bytes of transaction scratch per worker
+ * slot and 12 per bin, plus 81,920 bytes of transaction scratch per worker
  * at the first ck_txn_run.  Synchronous. */
 int ck_txn_create(ck_txn_table **out, uint64_t bins, uint32_t slots_per_bin, uint32_t trials, uint64_t seed);
 

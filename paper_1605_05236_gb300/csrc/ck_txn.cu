@@ -70,7 +70,7 @@ namespace {
 
 constexpr unsigned long long W_LOCK = 1ull, W_CLAIM = 2ull;
 constexpr int RS_MAX = 512;        // read-set entries per transaction
-constexpr int WS_MAX = 512;        // write-set entries per transaction
+constexpr int WS_MAX = 1024;       // write-set entries per transaction
 constexpr int HS = 2048;           // hash-set buckets per worker (power of two)
 constexpr int WORKERS_PER_BLOCK = 2;
 constexpr int CHAIN_SLOTS = 512;   // kick-out chain slots one insert plans (kicks <= 500)
@@ -85,6 +85,8 @@ constexpr int LOCK_POLLS = 1 << 15;
 // common.  Past this many the attempt aborts (TXS_ABORT_RS).
 constexpr int STAGE2_PASSES = 4096;
 constexpr uint32_t ATTEMPTS_MAX = 100000;
+constexpr uint32_t OVERFLOWS_MAX = 4;     // attempts that overflowed a read or write set before giving up
+constexpr uint32_t CHAIN_ABORTS_MAX = 64; // attempts that found no eligible slot for an insert
 constexpr uint64_t TIME_BUDGET_NS = 120ull * 1000 * 1000 * 1000;  // per worker and launch
 constexpr uint32_t BIN_KEY = 0x80000000u;  // hash-set keys: slot index, or bin index | BIN_KEY
 constexpr size_t SMEM_BYTES = (size_t)WORKERS_PER_BLOCK * HS * (8 + 4);
@@ -1011,7 +1013,7 @@ __global__ void __launch_bounds__(32 * WORKERS_PER_BLOCK) k_txn_run(
     const uint64_t base = tx * L;
     const uint64_t out = (uint64_t)trial * n_ops + base;
     int rc = 1;
-    uint32_t a = 0;
+    uint32_t a = 0, overflows = 0, chain_aborts = 0;
     unsigned long long tid = last, pos = ~0ull;
     while (rc == 1 && a < ATTEMPTS_MAX && now_ns() - start < TIME_BUDGET_NS) {
       a++;
@@ -1020,7 +1022,12 @@ __global__ void __launch_bounds__(32 * WORKERS_PER_BLOCK) k_txn_run(
                    value ? value + out : nullptr, tid, pos);
       if (rc == 1) {
         atomicAdd(t.stats + x.cause, 1ull);
-        if (a > 16) __nanosleep(64u << (a < 24 ? a - 16 : 8));
+        // a transaction too large for its read or write set overflows on
+        // every attempt, and one whose inserts cannot all be placed finds no
+        // eligible slot on every attempt: give those up
+        if (x.cause == TXS_ABORT_OVERFLOW && ++overflows == OVERFLOWS_MAX) rc = 2;
+        else if (x.cause == TXS_ABORT_CHAIN && ++chain_aborts == CHAIN_ABORTS_MAX) rc = 2;
+        else if (a > 16) __nanosleep(64u << (a < 24 ? a - 16 : 8));
       }
     }
     atomicAdd(t.stats + TXS_ATTEMPTS, (unsigned long long)a);

@@ -123,3 +123,52 @@ def test_txn_argument_errors_and_empty_call():
     tab.close()
     with pytest.raises(RuntimeError):
         txn.TxnTable(1 << 8, 5, 1)  # B must be 4 or 8
+
+
+@pytest.mark.parametrize("variant", ["local_retries", "claim_system"])
+def test_txn_four_slot_bins_match_serial_replay(variant):
+    flags = dict(txn.VARIANTS)[variant]
+    bins, B, W, L, trials, seed = 1 << 12, 4, 15, 64, 2, 5
+    work, tab, host = _run(flags, MIXES["delete_heavy"], bins, B, W, L, 0.9, trials, seed)
+    st_ref, val_ref, final_ref = otxn.replay(work)
+    s = tab.stats()
+    assert s["failed"] == 0, s
+    for r in range(trials):
+        _check_trial(work, tab, host, r, bins, B, seed, st_ref, val_ref, final_ref)
+    tab.close()
+
+
+def test_txn_that_cannot_fit_is_given_up():
+    """One worker fills a 2^10 x 8 table to 93.75% with 60 transactions of
+    128 inserts; then one transaction of 256 inserts asks for half of the
+    remaining free slots at once, through kick-out chains that only grow as
+    its own planned slots fill up: it overflows its write set (1024 entries:
+    2 per insert plus up to 2 per kick-out) or runs out of eligible slots.
+    Either way it is given up within a few dozen attempts (status 255
+    everywhere, nothing written) instead of retrying up to the attempt
+    bound, and the table keeps exactly the first 60 transactions' keys."""
+    bins, B = 1 << 10, 8
+    keys, _ = inputs.distinct_keys(7680 + 256, 17)
+    vals = inputs.values_for(keys)
+    flags = txn.LOCAL_RETRY | txn.CLAIM
+    tab = txn.TxnTable(bins, B, 1, seed=3)
+    tab.run(_dev(np.zeros(7680, np.uint8), np.uint8), _dev(keys[:7680], np.int32), _dev(vals[:7680], np.int32),
+            1, 60, 128, flags)
+    torch.cuda.synchronize()
+    s1 = tab.stats()
+    assert s1["failed"] == 0 and s1["commits"] == 60, s1
+    out = tab.run(_dev(np.zeros(256, np.uint8), np.uint8), _dev(keys[7680:], np.int32),
+                  _dev(vals[7680:], np.int32), 1, 1, 256, flags)
+    torch.cuda.synchronize()
+    s2 = tab.stats()
+    a = int(out["attempts"].item())
+    st = out["status"].cpu().numpy()
+    if s2["commits"] == 61:  # it fitted after all: then every insert went in
+        assert (st == 0).all(), s2
+        pytest.skip("the 256 inserts fitted; nothing to give up")
+    assert (st == 255).all()
+    assert s2["failed"] == 1 and a <= 64, (a, s2)
+    slots = tab.export(0)
+    stored = np.sort((slots[slots != np.uint64(0xFFFFFFFFFFFFFFFF)] >> np.uint64(32)).astype(np.uint32))
+    assert (stored == np.sort(keys[:7680])).all()
+    tab.close()
