@@ -203,6 +203,19 @@ int ck_clear(ck_table *t, void *stream);
  * counter).  Either pointer may be NULL. */
 int ck_export(ck_table *t, uint64_t *h_slots, uint32_t *h_meta);
 
+/* Restore a table from a snapshot ck_export wrote (synchronous): slots and
+ * meta in the layout above, from host memory, for a table of the same shape
+ * (the caller's responsibility; the sizes are this table's).  Checked first:
+ * no claim flag set (the snapshot must come from a table with no call in
+ * flight), duplicate marks only on occupied slots and an even number of
+ * them, no stored key 0xFFFFFFFF -- CK_EINVAL otherwise, and the table is
+ * left untouched.  Counters restart at zero except size and live ghost
+ * pairs, which are recomputed from the snapshot.  Spawn counts, hit
+ * counters, rattle counters and versions are restored as they were, so
+ * insertions continue exactly as they would have in the exported table
+ * (transaction IDs help logging and snapshots, Sec. 8). */
+int ck_import(ck_table *t, const uint64_t *h_slots, const uint32_t *h_meta);
+
 /* Free the table (and its memory, when ck_create allocated it). */
 void ck_destroy(ck_table *t);
 

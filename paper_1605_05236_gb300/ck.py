@@ -86,6 +86,7 @@ def load(build_if_missing: bool = True):
     L.ck_shape.argtypes = [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u32), ctypes.POINTER(_u32),
                            ctypes.POINTER(_u32)]
     L.ck_gather_probe.argtypes = [_vp, ctypes.c_size_t, _u32, _u64, _u64, _vp, _vp]
+    L.ck_import.argtypes = [_vp, _vp, _vp]
     L.ck_strerror.restype = ctypes.c_char_p
     L.ck_strerror.argtypes = [ctypes.c_int]
     _lib = L
@@ -248,6 +249,16 @@ class CuckooTable:
         _check(load().ck_export(self._h, slots.ctypes.data_as(ctypes.c_void_p),
                                 meta.ctypes.data_as(ctypes.c_void_p)), "ck_export")
         return slots, meta
+
+    def import_snapshot(self, slots: np.ndarray, meta: np.ndarray):
+        """ck_import: restore the slots and meta an export() of a table of
+        the same shape returned."""
+        slots = np.ascontiguousarray(slots, dtype=np.uint64)
+        meta = np.ascontiguousarray(meta, dtype=np.uint32)
+        if slots.size != self.bins * self.B or meta.size != self.bins:
+            raise ValueError("snapshot shape differs from the table's")
+        _check(load().ck_import(self._h, slots.ctypes.data_as(ctypes.c_void_p),
+                                meta.ctypes.data_as(ctypes.c_void_p)), "ck_import")
 
     def contents(self) -> dict:
         slots, _ = self.export()

@@ -522,6 +522,45 @@ int ck_export(ck_table* t, uint64_t* h_slots, uint32_t* h_meta) {
   return CK_OK;
 }
 
+int ck_import(ck_table* t, const uint64_t* h_slots, const uint32_t* h_meta) {
+  if (!t || !h_slots || !h_meta) return CK_EINVAL;
+  const uint64_t nb = t->dt.n_bins;
+  const uint32_t B = t->dt.B;
+  // a snapshot of a quiescent table: no claim flags, duplicate marks only on
+  // occupied slots and in pairs, no reserved key stored
+  uint64_t occupied = 0, dups = 0;
+  for (uint64_t b = 0; b < nb; b++) {
+    const uint32_t m = h_meta[b];
+    const uint32_t dmask = B > 1 ? (m >> DUP_SHIFT) & 0xFFu : 0u;
+    if (B > 1 ? (m & 0xFFu) != 0 : (m & 1u) != 0) return CK_EINVAL;
+    if (B > 1 && (dmask >> B) != 0) return CK_EINVAL;
+    for (uint32_t s = 0; s < B; s++) {
+      const uint64_t rec = h_slots[b * B + s];
+      const bool dup = (dmask >> s) & 1u;
+      if (rec == EMPTY) {
+        if (dup) return CK_EINVAL;
+        continue;
+      }
+      if ((uint32_t)(rec >> 32) == RESERVED_KEY) return CK_EINVAL;
+      occupied++;
+      dups += dup;
+    }
+  }
+  if (dups & 1) return CK_EINVAL;
+  if (cudaStreamSynchronize(t->last) != cudaSuccess) return CK_ECUDA;
+  if (cudaMemcpy(t->dt.slots, h_slots, t->dt.total_slots * sizeof(uint64_t), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(t->dt.meta, h_meta, nb * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(t->dt.counters, 0, COUNTER_WORDS * sizeof(uint64_t)) != cudaSuccess)
+    return CK_ECUDA;
+  // a ghost pair is one key stored twice, both copies marked
+  const unsigned long long size_ghosts[2] = {occupied - dups / 2, dups / 2};
+  static_assert(C_LIVE_GHOSTS == C_SIZE + 1, "size and live ghosts are adjacent counters");
+  if (cudaMemcpy(t->dt.counters + C_SIZE, size_ghosts, sizeof(size_ghosts), cudaMemcpyHostToDevice) != cudaSuccess)
+    return CK_ECUDA;
+  return CK_OK;
+}
+
 void ck_destroy(ck_table* t) {
   if (!t) return;
   if (t->last) cudaStreamSynchronize(t->last);

@@ -73,3 +73,8 @@ def test_txn_invalid_arguments_need_no_gpu():
     assert L.ck_txn_stats(None, None, 1) == ck.EINVAL
     assert L.ck_txn_export(None, 0, None) == ck.EINVAL
     L.ck_txn_destroy(None)
+
+
+def test_import_invalid_arguments_need_no_gpu():
+    L = ck.load()
+    assert L.ck_import(None, None, None) == ck.EINVAL
