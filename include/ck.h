@@ -477,6 +477,17 @@ int ck_txn_export(ck_txn_table *x, uint32_t trial, uint64_t *h_slots);
 
 void ck_txn_destroy(ck_txn_table *x);
 
+/* Testing aid (not an operation of the paper): set, then clear, claim
+ * flags of one bin directly (bits 0..B-1; bit 0 for single-slot bins).  A
+ * set flag stands in for an insertion that claimed the slot and never
+ * released it -- a writer that died mid-chain.  Every wait on a claim is
+ * bounded, so such a flag turns into per-key statuses, not a hang:
+ * insertions that need the slot end CK_ST_ABORTED after their claim
+ * retries, deletes of a key in it report 2, lookups are unaffected.
+ * Synchronous; call with no work on the table in flight.  CK_EINVAL for a
+ * bin out of range or a mask beyond the claim bits. */
+int ck_debug_claims(ck_table *t, uint64_t bin, uint32_t set_mask, uint32_t clear_mask);
+
 /* Measurement helper (not an operation of the paper): n_reads independent
  * random reads of `width` bytes (8, 32 or 64: one single-slot, 4-slot or
  * 8-slot bin) from a device buffer of `bytes` bytes (64-byte aligned), the

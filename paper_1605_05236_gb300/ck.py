@@ -87,6 +87,7 @@ def load(build_if_missing: bool = True):
                            ctypes.POINTER(_u32)]
     L.ck_gather_probe.argtypes = [_vp, ctypes.c_size_t, _u32, _u64, _u64, _vp, _vp]
     L.ck_import.argtypes = [_vp, _vp, _vp]
+    L.ck_debug_claims.argtypes = [_vp, _u64, _u32, _u32]
     L.ck_strerror.restype = ctypes.c_char_p
     L.ck_strerror.argtypes = [ctypes.c_int]
     _lib = L
@@ -259,6 +260,10 @@ class CuckooTable:
             raise ValueError("snapshot shape differs from the table's")
         _check(load().ck_import(self._h, slots.ctypes.data_as(ctypes.c_void_p),
                                 meta.ctypes.data_as(ctypes.c_void_p)), "ck_import")
+
+    def debug_claims(self, bin: int, set_mask: int = 0, clear_mask: int = 0):
+        """ck_debug_claims: set / clear claim flags of one bin (testing aid)."""
+        _check(load().ck_debug_claims(self._h, bin, set_mask, clear_mask), "ck_debug_claims")
 
     def contents(self) -> dict:
         slots, _ = self.export()

@@ -561,6 +561,17 @@ int ck_import(ck_table* t, const uint64_t* h_slots, const uint32_t* h_meta) {
   return CK_OK;
 }
 
+int ck_debug_claims(ck_table* t, uint64_t bin, uint32_t set_mask, uint32_t clear_mask) {
+  if (!t || bin >= t->dt.n_bins) return CK_EINVAL;
+  const uint32_t claim_bits = t->dt.B > 1 ? (1u << t->dt.B) - 1 : 1u;
+  if ((set_mask | clear_mask) & ~claim_bits) return CK_EINVAL;
+  if (cudaStreamSynchronize(t->last) != cudaSuccess) return CK_ECUDA;
+  uint32_t m = 0;
+  if (cudaMemcpy(&m, t->dt.meta + bin, sizeof(m), cudaMemcpyDeviceToHost) != cudaSuccess) return CK_ECUDA;
+  m = (m & ~clear_mask) | set_mask;
+  return cudaMemcpy(t->dt.meta + bin, &m, sizeof(m), cudaMemcpyHostToDevice) == cudaSuccess ? CK_OK : CK_ECUDA;
+}
+
 void ck_destroy(ck_table* t) {
   if (!t) return;
   if (t->last) cudaStreamSynchronize(t->last);

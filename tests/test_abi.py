@@ -78,3 +78,8 @@ def test_txn_invalid_arguments_need_no_gpu():
 def test_import_invalid_arguments_need_no_gpu():
     L = ck.load()
     assert L.ck_import(None, None, None) == ck.EINVAL
+
+
+def test_debug_claims_invalid_arguments_need_no_gpu():
+    L = ck.load()
+    assert L.ck_debug_claims(None, 0, 1, 0) == ck.EINVAL
