@@ -604,14 +604,29 @@ def job_rate(units_per_rank, steps, ms, world):
     return world * units_per_rank * steps / (ms * 1e-3) / 1e6
 
 
+# A collective that waits longer than this for a rank that is gone fails
+# with an error on the ranks still running, instead of holding their GPUs.
+PG_TIMEOUT_S = 300
+
+
+def init_ranks(backend, device=None, timeout_s=PG_TIMEOUT_S):
+    """The process group of a multi-rank run (rank and world from the
+    environment), with a bounded collective timeout."""
+    import datetime
+    import torch.distributed as dist
+    kw = {"timeout": datetime.timedelta(seconds=timeout_s)}
+    if device is not None:
+        kw["device_id"] = device
+    dist.init_process_group(backend, **kw)
+
+
 def run_gpu(args, rank, world, local):
     import torch
     from paper_1605_05236_gb300 import ck
 
     torch.cuda.set_device(local)
     if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        init_ranks("nccl", torch.device("cuda", local))
     ck.load()
     stream = torch.cuda.current_stream()
     seed = rank_seed(rank)

@@ -1,9 +1,12 @@
 """The multi-rank logic of bench.py on CPU: two gloo ranks, each with its
 own shard (seed), the job's time is the slowest rank's, and the job's rate
-counts every rank's units."""
+counts every rank's units; a rank that leaves between steps makes the
+survivor's next collective fail with an error within the process group's
+timeout instead of hanging."""
 import os
 import socket
 import sys
+import time
 
 import pytest
 import torch
@@ -48,6 +51,42 @@ def test_two_gloo_ranks_take_the_slowest_time_and_distinct_shards():
     out.sort()
     assert out[0][2] == out[1][2] == [11.0, 5.0, 2.0]
     assert out[0][1] != out[1][1]
+
+
+def _rank_leaves(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    bench.init_ranks("gloo", timeout_s=5)
+    bench.max_over_ranks(torch, [1.0], world, "cpu")  # one step together
+    if rank == 1:
+        q.put((rank, "left"))
+        q.close()
+        q.join_thread()
+        os._exit(0)  # gone between steps, without a goodbye
+    t0 = time.monotonic()
+    try:
+        bench.max_over_ranks(torch, [2.0], world, "cpu")
+        q.put((rank, "no error"))
+    except Exception as e:  # the collective gives up on the missing rank
+        q.put((rank, "error after %.1f s: %s" % (time.monotonic() - t0, type(e).__name__)))
+    q.close()
+    q.join_thread()
+    os._exit(0)
+
+
+@pytest.mark.timeout(120)
+def test_a_rank_that_leaves_fails_the_next_collective():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_leaves, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = dict(q.get(timeout=100) for _ in range(world))
+    for p in procs:
+        p.join(timeout=30)
+    assert out[1] == "left"
+    assert out[0].startswith("error after"), out[0]
+    assert float(out[0].split()[2]) < 60
 
 
 def test_job_rate_counts_every_rank():
