@@ -762,9 +762,9 @@ def end_to_end(torch, ck, table, keys, vals, lk, dk, stream, K):
     """The same metric through the public API from pinned host buffers.
 
     `value`: the fill alone, as `value` of the bench line counts it, with
-    its copies inside the timed region: each batch's keys and values come
-    in on a second stream while the batch before it is inserted, and the
-    statuses go out at the end.  `whole_step`: the whole step (fill,
+    its copies inside the timed region: keys and values come in on a second
+    stream in chunks of 1, 2, 4, ... batches while the chunk before is
+    inserted, and each chunk's statuses go out once it is inserted.  `whole_step`: the whole step (fill,
     lookups, deletes) the same way, with the lookup and delete keys copied
     in during the fill and every result copied out -- inserts per second of
     the whole step, the same unit over more work.  Both are how a caller of
@@ -788,13 +788,22 @@ def end_to_end(torch, ck, table, keys, vals, lk, dk, stream, K):
     ddf = torch.empty(len(dk), dtype=torch.uint8, device="cuda")
     cs = torch.cuda.Stream()  # copies
     bounds = [(lo, min(n, lo + BATCH)) for lo in range(0, n, BATCH)]
+    # batches grouped into chunks of 1, 2, 4, ... batches: the insert stream
+    # waits for a chunk's copy once, so consecutive insert launches inside a
+    # chunk still overlap, while the first launch waits for one batch only
+    chunks, i, size = [], 0, 1
+    while i < len(bounds):
+        chunks.append(bounds[i:i + size])
+        i += size
+        size *= 2
 
     def step(whole):
         cs.wait_stream(stream)
         table.clear(stream)
         copied = []
         with torch.cuda.stream(cs):
-            for lo, hi in bounds:  # every batch in order, each with its own event
+            for ch in chunks:  # every chunk in order, each with its own event
+                lo, hi = ch[0][0], ch[-1][1]
                 dkey[lo:hi].copy_(hk[lo:hi], non_blocking=True)
                 dval[lo:hi].copy_(hv[lo:hi], non_blocking=True)
                 e = torch.cuda.Event()
@@ -805,11 +814,19 @@ def end_to_end(torch, ck, table, keys, vals, lk, dk, stream, K):
                 ddk.copy_(hd, non_blocking=True)
                 keys_in = torch.cuda.Event()
                 keys_in.record(cs)
-        for (lo, hi), e in zip(bounds, copied):
+        done = []
+        for ch, e in zip(chunks, copied):
             stream.wait_event(e)
-            table.insert_batch(dkey[lo:hi], dval[lo:hi], dst[lo:hi], stream)
-        ins_done = torch.cuda.Event()
-        ins_done.record(stream)
+            for lo, hi in ch:
+                table.insert_batch(dkey[lo:hi], dval[lo:hi], dst[lo:hi], stream)
+            d = torch.cuda.Event()
+            d.record(stream)
+            done.append(d)
+        with torch.cuda.stream(cs):  # each chunk's statuses go out once it is inserted
+            for ch, d in zip(chunks[:-1], done[:-1]):
+                cs.wait_event(d)
+                hst[ch[0][0]:ch[-1][1]].copy_(dst[ch[0][0]:ch[-1][1]], non_blocking=True)
+        ins_done = done[-1]
         if whole:
             stream.wait_event(keys_in)
             table.lookup(dl, dlv, dlf, stream)
@@ -820,7 +837,8 @@ def end_to_end(torch, ck, table, keys, vals, lk, dk, stream, K):
             del_done.record(stream)
         with torch.cuda.stream(cs):
             cs.wait_event(ins_done)
-            hst.copy_(dst, non_blocking=True)
+            last = chunks[-1]
+            hst[last[0][0]:last[-1][1]].copy_(dst[last[0][0]:last[-1][1]], non_blocking=True)
             if whole:
                 cs.wait_event(lk_done)
                 hlv.copy_(dlv, non_blocking=True)
