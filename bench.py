@@ -564,23 +564,53 @@ def txn_form(torch, stream):
     return res
 
 
+def host_info():
+    """Core count and CPU model of this host."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                if k.strip() in ("model name", "CPU part") and v.strip():
+                    model = (k.strip() + " " + v.strip()) if k.strip() == "CPU part" else v.strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "cpu": model}
+
+
 def cpu_baseline():
     """The oracle, as it stands, on one host core: a bounded sample of the
-    workload (a 2^22-bin x 4-slot table filled to 0.95 with queue-kicking)."""
+    workload (a 2^22-bin x 4-slot table filled to 0.95 with queue-kicking,
+    then 2^22 lookups at 50% hits and 2^20 deletes of present keys).  The
+    oracle is serial (its batch calls keep counters), so every leg uses one
+    core."""
     import oracle
     from paper_1605_05236_gb300 import inputs
     bins = 1 << 22
     n = inputs.load_target(bins * B, LOAD)
-    keys, _ = inputs.distinct_keys(n, 1)
+    keys, nxt = inputs.distinct_keys(n, 1)
     vals = inputs.values_for(keys)
+    lk, _ = inputs.lookup_keys(keys, 1 << 22, 1, 0.5, next_start=nxt)
+    dk = inputs.delete_keys(keys, 1 << 20, 1)
     t = oracle.OracleTable(bins, B, 2, oracle.QUEUE, rng_seed=1, cap=500)
     t0 = time.perf_counter()
     t.insert(keys, vals)
     dt = time.perf_counter() - t0
     s = t.stats()
+    t0 = time.perf_counter()
+    t.lookup(lk)
+    dl = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    t.delete(dk)
+    dd = time.perf_counter() - t0
     return {"value": round(n / dt / 1e6, 3), "unit": "M inserts/s", "cores": 1, "kind": "oracle",
             "sample": "serial C oracle, queue-kicking fill of a 2^22-bin x 4-slot table from empty to 0.95 "
-                      "(%d keys, %.1f s); bins viewed/insert %.4f" % (n, dt, s["bins_viewed"] / n)}
+                      "(%d keys, %.1f s); bins viewed/insert %.4f; then %d lookups (50%% hits) and %d deletes "
+                      "of present keys on the filled table" % (n, dt, s["bins_viewed"] / n, len(lk), len(dk)),
+            "m_lookups_per_s": round(len(lk) / dl / 1e6, 3), "m_deletes_per_s": round(len(dk) / dd / 1e6, 3),
+            "host": host_info()}
 
 
 def rank_seed(rank: int) -> int:
@@ -914,7 +944,7 @@ def run_reference(args, rank, world):
             "dtype": "u32 keys/values in u64 slots (integer)", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": sample},
             "cpu_baseline": {"value": round(value, 3), "unit": "M inserts/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "host": host_info()},
             "e2e": {"value": round(value, 3), "unit": "M inserts/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
