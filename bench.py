@@ -173,6 +173,26 @@ def gather_roofline(torch, ck, nbytes, width, n_reads, stream):
     return n_reads * width / (best * 1e-3) / 1e9
 
 
+def atomic_rate(torch, ck, nbytes, kind, n_ops, stream):
+    """Measured random atomics (G ops/s) of `kind` (ck_atomic_probe) over a
+    buffer of `nbytes`."""
+    buf = torch.zeros(nbytes // 8, dtype=torch.int64, device="cuda")
+    sink = torch.zeros(1024, dtype=torch.int64, device="cuda")
+    for i in range(3):
+        ck.atomic_probe(buf, kind, n_ops, 17 + i, sink, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = None
+    for i in range(5):
+        e0.record(stream)
+        ck.atomic_probe(buf, kind, n_ops, 100 + i, sink, stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del buf
+    return n_ops / (best * 1e-3) / 1e9
+
+
 def fill_once(torch, ck, table, kt, vt, st, stream, batch=BATCH):
     """Fill from empty in `batch`-key calls; returns (ms, per-launch ms list)."""
     n = kt.numel()
@@ -747,6 +767,19 @@ def run_gpu(args, rank, world, local):
                 "traffic_unit": "bytes per launch (mean DRAM read + write of one fill's 61 launches, ncu)",
                 "bytes_per_launch": int(bytes_per_launch), "avg_launch_ms": round(avg_launch_ms, 4),
                 "vs_random_gather_32B": {"gbs": round(g32, 1), "frac": round(achieved / g32, 4)}}
+    # the random-operation model of a low-load launch: a key reads its two
+    # bins' 32-B slot sectors, writes one slot by a 64-bit compare-and-swap
+    # and updates its bin's metadata word by a 32-bit add, each class at its
+    # measured rate over an array of the table's size
+    red = atomic_rate(torch, ck, BINS * 4, 0, 1 << 26, stream)   # metadata words
+    cas = atomic_rate(torch, ck, BINS * B * 8, 2, 1 << 26, stream)  # slots
+    model_ms = BATCH * (2 * 32 / (g32 * 1e9) + 1 / (cas * 1e9) + 1 / (red * 1e9)) * 1e3
+    first_ms = profile["launch_ms_at_load"]["0.000"]
+    roofline["random_ops_model"] = {
+        "gather32_g_per_s": round(g32 / 32, 2), "cas64_g_per_s": round(cas, 2), "red32_g_per_s": round(red, 2),
+        "first_launch_ms": first_ms, "model_ms": round(model_ms, 4), "frac": round(model_ms / first_ms, 4),
+        "note": "first 2^20-key launch (load 0 to 0.016, serialised) against 2 random 32-B reads + 1 random "
+                "64-bit CAS + 1 random 32-bit add per key at the probes' measured rates"}
     roof_lookup = {"kernel": "k_lookup2<4>", "bound": "hbm", "achieved": round(look_gbs, 1), "peak": hbm,
                    "unit": "GB/s", "frac": round(look_gbs / hbm, 4),
                    "bytes_per_lookup": 73, "vs_random_gather_32B": {"gbs": round(g32, 1),

@@ -497,6 +497,16 @@ int ck_debug_claims(ck_table *t, uint64_t bin, uint32_t set_mask, uint32_t clear
 int ck_gather_probe(const void *d_buf, size_t bytes, uint32_t width, uint64_t n_reads,
                     uint64_t seed, void *d_sink, void *stream);
 
+/* Measurement helper (not an operation of the paper): n_ops independent
+ * random atomics over a device buffer of `bytes` bytes (64-byte aligned),
+ * the read-modify-writes insertions issue.  kind 0: a 32-bit add with no
+ * result (red; a metadata update); 1: a 32-bit add whose result is used
+ * (a claim-style round trip); 2: a 64-bit compare-and-swap whose result is
+ * used (a slot write).  The buffer's contents change.  d_sink: 8 KB of
+ * device memory the kernel may write.  Asynchronous. */
+int ck_atomic_probe(void *d_buf, size_t bytes, uint32_t kind, uint64_t n_ops, uint64_t seed,
+                    void *d_sink, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,6 +86,7 @@ def load(build_if_missing: bool = True):
     L.ck_shape.argtypes = [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u32), ctypes.POINTER(_u32),
                            ctypes.POINTER(_u32)]
     L.ck_gather_probe.argtypes = [_vp, ctypes.c_size_t, _u32, _u64, _u64, _vp, _vp]
+    L.ck_atomic_probe.argtypes = [_vp, ctypes.c_size_t, _u32, _u64, _u64, _vp, _vp]
     L.ck_import.argtypes = [_vp, _vp, _vp]
     L.ck_debug_claims.argtypes = [_vp, _u64, _u32, _u32]
     L.ck_strerror.restype = ctypes.c_char_p
@@ -285,3 +286,11 @@ def gather_probe(buf: torch.Tensor, width: int, n_reads: int, seed: int, sink: t
     rc = load().ck_gather_probe(_ptr(buf), buf.numel() * buf.element_size(), width, n_reads, seed,
                                 _ptr(sink), _stream(stream))
     _check(rc, "ck_gather_probe")
+
+
+def atomic_probe(buf: torch.Tensor, kind: int, n_ops: int, seed: int, sink: torch.Tensor, stream=None):
+    """Random atomics on `buf` (see ck_atomic_probe; kind 0: red.add.u32,
+    1: atom.add.u32, 2: atom.cas.b64)."""
+    rc = load().ck_atomic_probe(_ptr(buf), buf.numel() * buf.element_size(), kind, n_ops, seed,
+                                _ptr(sink), _stream(stream))
+    _check(rc, "ck_atomic_probe")

@@ -1,7 +1,10 @@
-// ck_probe.cu -- random-gather microbenchmark: the measured roofline for
-// the table's access pattern (independent random reads of one sector-sized
-// record: 8 B for a single-slot bin, 32 B for a 4-slot bin, 64 B for an
-// 8-slot bin) over a buffer the size of the table.
+// ck_probe.cu -- random-access microbenchmarks: the measured rooflines for
+// the table's access patterns over a buffer the size of the table.
+// Gathers: independent random reads of one sector-sized record (8 B for a
+// single-slot bin, 32 B for a 4-slot bin, 64 B for an 8-slot bin).
+// Atomics: independent random read-modify-writes of the kinds insertions
+// issue (a fire-and-forget 32-bit add on a metadata word, a returning
+// 32-bit add, a returning 64-bit compare-and-swap on a slot).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -55,7 +58,59 @@ __global__ void __launch_bounds__(256) k_gather(const uint64_t* __restrict__ buf
   if (acc == 0x0123456789ABCDEFull) sink[tid & 1023] = acc;  // keeps the loads live
 }
 
+// KIND 0: red.add.u32 (no result), 1: atom.add.u32 (result used),
+// 2: atom.cas.b64 against 0 on an all-ones-free buffer (result used).
+template <int KIND>
+__global__ void __launch_bounds__(256) k_atomic(uint64_t* __restrict__ buf, uint64_t n_words, uint64_t mask,
+                                                uint64_t n_ops, uint64_t seed, uint64_t* __restrict__ sink) {
+  constexpr int U = 8;  // independent operations in flight per thread
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t acc = 0;
+  for (uint64_t i = tid * U; i < n_ops; i += stride * U) {
+    uint64_t v[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      v[u] = 0;
+      if (i + u >= n_ops) continue;
+      const uint64_t h = mix64(seed ^ (i + u));
+      const uint64_t r = mask ? (h & mask) : h % n_words;
+      if constexpr (KIND == 0) {
+        unsigned int* p = reinterpret_cast<unsigned int*>(buf) + r;
+        asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(p) : "memory");
+      } else if constexpr (KIND == 1) {
+        unsigned int* p = reinterpret_cast<unsigned int*>(buf) + r;
+        v[u] = atomicAdd(p, 1u);
+      } else {
+        v[u] = atomicCAS(reinterpret_cast<unsigned long long*>(buf) + r, 0ull, 1ull);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) acc ^= v[u];
+  }
+  if (acc == 0x0123456789ABCDEFull) sink[tid & 1023] = acc;  // keeps the results live
+}
+
 }  // namespace
+
+extern "C" int ck_atomic_probe(void* d_buf, size_t bytes, uint32_t kind, uint64_t n_ops, uint64_t seed,
+                               void* d_sink, void* stream) {
+  if (!d_buf || !d_sink || kind > 2) return CK_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(d_buf) % 64) != 0 || bytes < 64) return CK_EINVAL;
+  const uint64_t word = kind == 2 ? 8 : 4;
+  const uint64_t n_words = bytes / word;
+  const uint64_t mask = (n_words & (n_words - 1)) == 0 ? n_words - 1 : 0;
+  uint64_t grid = ((n_ops + 7) / 8 + 255) / 256;
+  if (grid > 152ull * 64) grid = 152ull * 64;
+  if (grid == 0) grid = 1;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  uint64_t* b = static_cast<uint64_t*>(d_buf);
+  uint64_t* k = static_cast<uint64_t*>(d_sink);
+  if (kind == 0) k_atomic<0><<<(unsigned)grid, 256, 0, s>>>(b, n_words, mask, n_ops, seed, k);
+  else if (kind == 1) k_atomic<1><<<(unsigned)grid, 256, 0, s>>>(b, n_words, mask, n_ops, seed, k);
+  else k_atomic<2><<<(unsigned)grid, 256, 0, s>>>(b, n_words, mask, n_ops, seed, k);
+  return cudaGetLastError() == cudaSuccess ? CK_OK : CK_ECUDA;
+}
 
 extern "C" int ck_gather_probe(const void* d_buf, size_t bytes, uint32_t width, uint64_t n_reads,
                                uint64_t seed, void* d_sink, void* stream) {
