@@ -1,0 +1,71 @@
+"""Parity at the benchmark's full size and launch configuration: the
+workload of bench.py (a 2^24-bin x 4-slot table filled from empty to load
+0.95 with queue-kicking in 61 calls of 2^20 keys on one stream, launches
+overlapping, then 2^26 lookups at 50% hits and 2^22 deletes of present
+keys).  The oracle fills the same table serially; the concurrent GPU fill
+must hold exactly the same key -> value set (compared over all 63,753,420
+records), satisfy every table invariant, view bins within 10% of the
+serial oracle, answer every lookup as the workload fixes it, and delete
+every deleted key."""
+import os
+import sys
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1605_05236_gb300 import ck, inputs
+
+from table_checks import check_table
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+EMPTY = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def _sorted_records(slots):
+    r = slots[slots != EMPTY]
+    r.sort()
+    return r
+
+
+@pytest.mark.timeout(900)
+def test_full_size_fill_lookups_deletes_match_the_oracle():
+    keys, vals, lk, expect, dk = bench.workload(bench.rank_seed(0))
+    n = len(keys)
+    t = ck.CuckooTable(bench.BINS, bench.B, 2, ck.QUEUE, seed=bench.rank_seed(0))
+    kt, vt = ck.as_u32_tensor(keys), ck.as_u32_tensor(vals)
+    st = torch.empty(n, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream()
+    for lo in range(0, n, bench.BATCH):  # the benchmark's calls, back to back on one stream
+        t.insert_batch(kt[lo:lo + bench.BATCH], vt[lo:lo + bench.BATCH], st[lo:lo + bench.BATCH], s)
+    torch.cuda.synchronize()
+    assert (st == 0).all().item()
+    slots, meta = t.export()
+    info = check_table(slots, meta, bench.BINS, bench.B, 2)
+    assert info["size"] == n and info["ghost_pairs"] == 0
+    gs = t.stats()
+    assert gs["size"] == n and gs["inserts_ok"] == n
+
+    ref = oracle.OracleTable(bench.BINS, bench.B, 2, oracle.QUEUE, rng_seed=bench.rank_seed(0), cap=500)
+    ost = ref.insert(keys, vals)
+    assert (ost == 0).all()
+    assert np.array_equal(_sorted_records(slots), _sorted_records(ref.export()["rec"]))
+    ratio = gs["bins_viewed_all"] / ref.stats()["bins_viewed"]
+    assert 0.90 < ratio < 1.10, ratio
+    del ref
+
+    v, f = t.lookup(ck.as_u32_tensor(lk))
+    f = f.cpu().numpy().astype(bool)
+    assert np.array_equal(f, expect.astype(bool))
+    assert np.array_equal(ck.u32_numpy(v)[f], inputs.values_for(lk[f]))
+    fd = t.delete(ck.as_u32_tensor(dk)).cpu().numpy()
+    assert (fd == 1).all()
+    _, f2 = t.lookup(ck.as_u32_tensor(dk))
+    assert not f2.cpu().numpy().any()
+    assert t.stats()["size"] == n - len(dk)
