@@ -283,7 +283,9 @@ def policy_fills(torch, ck, stream, base_keys):
             ("random_d4_0.96_hash1", 1 << 26, 1, 4, ck.RANDOM | 0x10000, 0.96, 4096),
             ("rattle_d4_0.96_hash1", 1 << 26, 1, 4, ck.RATTLE | 0x10000, 0.96, 500),
             ("sorted_d4_0.96", 1 << 26, 1, 4, ck.SORTED, 0.96, 500),
-            ("hybrid_d4_0.96", 1 << 26, 1, 4, ck.HYBRID, 0.96, 500)):
+            ("hybrid_d4_0.96", 1 << 26, 1, 4, ck.HYBRID, 0.96, 500),
+            ("sorted_d4_0.96_hash1", 1 << 26, 1, 4, ck.SORTED | 0x10000, 0.96, 500),
+            ("hybrid_d4_0.96_hash1", 1 << 26, 1, 4, ck.HYBRID | 0x10000, 0.96, 500)):
         n = inputs.load_target(bins * b, load)
         keys, nxt = inputs.distinct_keys(n, 2)
         kt, vt = ck.as_u32_tensor(keys), ck.as_u32_tensor(inputs.values_for(keys))
