@@ -179,7 +179,7 @@ void free_slots(ck_server* s) {
   s->slots.clear();
 }
 
-void complete(ck_server* s, Request* r, int64_t t) {
+void complete(Request* r, int64_t t) {
   r->t_done = t;
   r->done.store(1, std::memory_order_release);
 }
@@ -256,7 +256,7 @@ void scheduler_loop(ck_server* s) {
           if ((uint64_t)(t - r->t_arrive) > s->cfg.max_defer_us * 1000ull) {
             if (r->status_out) std::memset(r->status_out, CK_ST_BUSY, r->n);
             s->busy_rejects++;
-            complete(s, r, t);
+            complete(r, t);
             return true;
           }
           still.push_back(r);
@@ -333,7 +333,7 @@ void completer_loop(ck_server* s) {
         } else if (r->op == CK_OP_DELETE) {
           for (uint64_t k = 0; k < r->n; k++) d_live -= st[k] == 1;
         }
-        complete(s, r, t);
+        complete(r, t);
       }
     }
     std::lock_guard<std::mutex> lk(s->mu);
@@ -447,7 +447,7 @@ int ck_server_submit(ck_server* s, uint32_t op, const uint32_t* h_keys, const ui
   r->done.store(0);
   *ticket = r;
   if (n == 0) {
-    complete(s, r, now_ns());
+    complete(r, now_ns());
     return CK_OK;
   }
   {

@@ -4,8 +4,6 @@ import ctypes
 import os
 import re
 
-import pytest
-
 from paper_1605_05236_gb300 import build as ckbuild
 from paper_1605_05236_gb300 import ck
 
