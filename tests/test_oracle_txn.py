@@ -66,3 +66,49 @@ def test_workload_fill_to_keeps_a_prefix_of_each_worker():
         b = slice(w * T * L, w * T * L + t * L)
         assert (cut["op"][a] == full["op"][b]).all() and (cut["key"][a] == full["key"][b]).all()
         assert (cut["val"][a] == full["val"][b]).all()
+
+
+def _run_order(work, order, L):
+    """Apply whole transactions in `order` to a dict; per-op results."""
+    op, key, val = work["op"], work["key"], work["val"]
+    st = np.zeros(len(op), dtype=np.uint8)
+    v = np.zeros(len(op), dtype=np.uint32)
+    table = {}
+    for tx in order:
+        for i in range(tx * L, (tx + 1) * L):
+            k, o = int(key[i]), int(op[i])
+            if o == I:
+                table[k] = int(val[i])
+            elif k in table:
+                st[i] = 1
+                if o == R:
+                    v[i] = table[k]
+                elif o == O:
+                    table[k] = int(val[i])
+                else:
+                    del table[k]
+    return st, v, table
+
+
+def test_every_serial_order_of_the_workload_gives_the_replay():
+    """The premise of the GPU comparison: workers own their keys, so any
+    serial order of whole transactions that keeps each worker's own order
+    (every serializable execution) gives each operation the replay's result
+    and the same final map."""
+    W, T, L = 4, 12, 6
+    work = inputs.txn_workload(W, T, L, (2, 1, 2, 2), seed=9)
+    st_ref, v_ref, final_ref = txn.replay(work)
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        # a random interleaving: draw the worker of each next transaction
+        left = [list(range(w * T, (w + 1) * T)) for w in range(W)]
+        order = []
+        while any(left):
+            w = rng.choice([i for i in range(W) if left[i]])
+            order.append(left[w].pop(0))
+        st, v, final = _run_order(work, order, L)
+        assert np.array_equal(st, st_ref) and np.array_equal(v, v_ref) and final == final_ref
+    # and a worker's own order matters: reversing one worker's transactions changes results
+    order = list(range(T))[::-1] + list(range(T, W * T))
+    st, _, _ = _run_order(work, order, L)
+    assert not np.array_equal(st, st_ref)
