@@ -240,6 +240,18 @@ def chain_summary(hist):
             "p999": int(lo[np.searchsorted(cdf, 0.999)]), "zero_kick_share": round(float(hist[0] / total), 4)}
 
 
+def viewed_curve(t, points=(0.5, 0.7, 0.8, 0.9, 0.95)):
+    """Bins viewed per insertion at each density (Sec. 3's metric, the
+    curves of Figs. A-C): the insertions of the last fill that started in
+    the 0.5%-wide load bucket just below the density."""
+    v, c = t.load_histogram()
+    out = {}
+    for q in points:
+        b = min(len(c) - 1, max(0, int(round(q * len(c))) - 1))
+        out["%.2f" % q] = round(float(v[b]) / float(c[b]), 3) if c[b] else None
+    return out
+
+
 def policy_fills(torch, ck, stream, base_keys):
     """One fill per policy on the same shapes (the policy rows of the path)."""
     from paper_1605_05236_gb300 import inputs
@@ -262,6 +274,7 @@ def policy_fills(torch, ck, stream, base_keys):
         s = t.stats()
         out[name] = {"table": "2^24x4", "load": LOAD, "m_inserts_per_s": round(len(keys) / ms / 1e3, 2),
                      "bins_viewed_per_insert": round(s["bins_viewed_per_insert"], 4),
+                     "viewed_by_load": viewed_curve(t),
                      "kicks_per_insert": round(s["kicks"] / max(1, s["inserts_ok"]), 4),
                      "chain_max": s["chain_max"], "chain": chain_summary(t.chain_histogram()),
                      "failed": s["inserts_failed"], "aborted": s["inserts_aborted"],
@@ -301,6 +314,8 @@ def policy_fills(torch, ck, stream, base_keys):
                "hash_family": family,
                "m_inserts_per_s": round(n / ms / 1e3, 2),
                "bins_viewed_per_insert": round(s["bins_viewed_per_insert"], 4),
+               "viewed_by_load": viewed_curve(t, tuple(q for q in (0.5, 0.7, 0.8, 0.9, 0.95, 0.96, 0.97, 0.99)
+                                                       if q <= load)),
                "chain_max": s["chain_max"], "chain": chain_summary(t.chain_histogram()),
                "failed": s["inserts_failed"], "aborted": s["inserts_aborted"]}
         if d > 2:
