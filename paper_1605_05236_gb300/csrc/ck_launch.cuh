@@ -1,0 +1,87 @@
+// ck_launch.cuh -- host-side launch of the insert kernel, shared by the
+// translation units that instantiate it (ck_insert_b1.cu, ck_insert_b4.cu,
+// ck_insert_b8.cu: one bin size each, so they compile in parallel).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "ck.h"
+#include "ck_kernels.cuh"
+
+namespace ck {
+
+// The host-side parameters of one insert launch (a table handle's fields).
+struct InsertLaunch {
+  const DevTable* dt;
+  uint32_t block;
+  int sm_count;
+  bool overlap;          // the launch may start while its predecessor finishes
+  uint64_t load_base;    // keys already in the table (the bins-viewed histogram's load)
+  uint64_t max_threads;  // insertions in flight at most
+};
+
+using InsertFn = cudaError_t (*)(const InsertLaunch& l, const uint32_t* keys, const uint32_t* vals, uint64_t n,
+                                 uint8_t* st, uint32_t* viewed, bool serial, uint32_t upsert, cudaStream_t s);
+
+// The launch function for a policy, or nullptr (one definition per bin size).
+InsertFn pick_insert_b1(uint32_t policy);
+InsertFn pick_insert_b4(uint32_t policy, bool ghost);
+InsertFn pick_insert_b8(uint32_t policy, bool ghost);
+
+template <int B, int POL, bool GHOST>
+cudaError_t launch_insert(const InsertLaunch& l, const uint32_t* keys, const uint32_t* vals, uint64_t n,
+                          uint8_t* st, uint32_t* viewed, bool serial, uint32_t upsert, cudaStream_t s) {
+  const DevTable& dt = *l.dt;
+  const uint64_t load_base = l.load_base;
+  if (serial) {
+    k_insert<B, POL, GHOST, true><<<1, 1, 0, s>>>(dt, keys, vals, n, st, viewed, load_base, upsert);
+    return cudaGetLastError();
+  }
+  const uint32_t block = l.block;
+  // persistent launch: at most the blocks that fit on the GPU at once
+  static int cached_block = 0, cached_per_sm = 0;
+  if (cached_block != (int)block) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_insert<B, POL, GHOST, false>, block, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    cached_per_sm = per_sm;
+    cached_block = (int)block;
+  }
+  uint64_t grid = (n + block - 1) / block;
+  uint64_t resident = (uint64_t)cached_per_sm * l.sm_count;
+  if (grid > resident) grid = resident;
+  uint64_t by_threads = l.max_threads / block;  // insertions in flight at once
+  if (grid > by_threads) grid = by_threads > 0 ? by_threads : 1;
+  if (dt.scratch) {
+    uint64_t cap_blocks = dt.n_searchers / SLAB;
+    if (grid > cap_blocks) grid = cap_blocks;
+  }
+  if (grid > 0x7FFFFFFFull) grid = 0x7FFFFFFFull;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = l.overlap ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_insert<B, POL, GHOST, false>, dt, keys, vals, n, st, viewed, load_base, upsert);
+}
+
+// The two-choice policies for one bin size.
+template <int B>
+InsertFn pick_two_choice(uint32_t pol, bool ghost) {
+  switch (pol) {
+    case CK_RANDOM: return ghost ? launch_insert<B, P_RANDOM, true> : launch_insert<B, P_RANDOM, false>;
+    case CK_BFS: return ghost ? launch_insert<B, P_BFS, true> : launch_insert<B, P_BFS, false>;
+    case CK_SORTED: return ghost ? launch_insert<B, P_SORTED, true> : launch_insert<B, P_SORTED, false>;
+    case CK_HYBRID: return ghost ? launch_insert<B, P_HYBRID, true> : launch_insert<B, P_HYBRID, false>;
+    case CK_QUEUE: return ghost ? launch_insert<B, P_QUEUE, true> : launch_insert<B, P_QUEUE, false>;
+    default: return nullptr;
+  }
+}
+
+}  // namespace ck

@@ -8,7 +8,7 @@
 #include <new>
 
 #include "ck.h"
-#include "ck_kernels.cuh"
+#include "ck_launch.cuh"
 
 using namespace ck;
 
@@ -163,83 +163,11 @@ int init_table(ck_table* t, void* buf, size_t bytes, bool owns, uint64_t bins, u
 
 // ---- kernel dispatch -------------------------------------------------
 
-template <int B, int POL, bool GHOST>
-cudaError_t launch_insert_dt(const DevTable& dt, uint32_t block, int sm_count, bool overlap, uint64_t load_base,
-                             const uint32_t* keys, const uint32_t* vals, uint64_t n, uint8_t* st, uint32_t* viewed,
-                             bool serial, cudaStream_t s, uint64_t max_threads = ~0ull, uint32_t upsert = 0) {
-  if (serial) {
-    k_insert<B, POL, GHOST, true><<<1, 1, 0, s>>>(dt, keys, vals, n, st, viewed, load_base, upsert);
-    return cudaGetLastError();
-  }
-  // persistent launch: at most the blocks that fit on the GPU at once
-  static int cached_block = 0, cached_per_sm = 0;
-  if (cached_block != (int)block) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_insert<B, POL, GHOST, false>, block, 0) !=
-            cudaSuccess ||
-        per_sm < 1)
-      per_sm = 1;
-    cached_per_sm = per_sm;
-    cached_block = (int)block;
-  }
-  uint64_t grid = (n + block - 1) / block;
-  uint64_t resident = (uint64_t)cached_per_sm * sm_count;
-  if (grid > resident) grid = resident;
-  uint64_t by_threads = max_threads / block;  // insertions in flight at once
-  if (grid > by_threads) grid = by_threads > 0 ? by_threads : 1;
-  if (dt.scratch) {
-    uint64_t cap_blocks = dt.n_searchers / SLAB;
-    if (grid > cap_blocks) grid = cap_blocks;
-  }
-  if (grid > 0x7FFFFFFFull) grid = 0x7FFFFFFFull;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = overlap ? 1 : 0;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_insert<B, POL, GHOST, false>, dt, keys, vals, n, st, viewed, load_base, upsert);
-}
-
-template <int B, int POL, bool GHOST>
-cudaError_t launch_insert(const ck_table* t, const uint32_t* keys, const uint32_t* vals, uint64_t n, uint8_t* st,
-                          uint32_t* viewed, bool serial, uint32_t upsert, cudaStream_t s) {
-  return launch_insert_dt<B, POL, GHOST>(t->dt, t->block, t->sm_count, t->overlap != 0, t->load_base, keys, vals,
-                                         n, st, viewed, serial, s, ~0ull, upsert);
-}
-
-using InsertFn = cudaError_t (*)(const ck_table*, const uint32_t*, const uint32_t*, uint64_t, uint8_t*,
-                                 uint32_t*, bool, uint32_t, cudaStream_t);
-
-template <int B>
-InsertFn pick_two_choice(uint32_t pol, bool ghost) {
-  switch (pol) {
-    case CK_RANDOM: return ghost ? launch_insert<B, P_RANDOM, true> : launch_insert<B, P_RANDOM, false>;
-    case CK_BFS: return ghost ? launch_insert<B, P_BFS, true> : launch_insert<B, P_BFS, false>;
-    case CK_SORTED: return ghost ? launch_insert<B, P_SORTED, true> : launch_insert<B, P_SORTED, false>;
-    case CK_HYBRID: return ghost ? launch_insert<B, P_HYBRID, true> : launch_insert<B, P_HYBRID, false>;
-    case CK_QUEUE: return ghost ? launch_insert<B, P_QUEUE, true> : launch_insert<B, P_QUEUE, false>;
-    default: return nullptr;
-  }
-}
-
 InsertFn pick_insert(const ck_table* t) {
   const DevTable& d = t->dt;
-  if (d.B == 1) {
-    switch (d.policy) {
-      case CK_RATTLE: return launch_insert<1, P_RATTLE, false>;
-      case CK_BFS: return launch_insert<1, P_BFS, false>;
-      case CK_SORTED: return launch_insert<1, P_SORTED, false>;
-      case CK_HYBRID: return launch_insert<1, P_HYBRID, false>;
-      default: return launch_insert<1, P_RANDOM, false>;
-    }
-  }
-  if (d.B == 4) return pick_two_choice<4>(d.policy, d.ghost != 0);
-  if (d.B == 8) return pick_two_choice<8>(d.policy, d.ghost != 0);
+  if (d.B == 1) return pick_insert_b1(d.policy);
+  if (d.B == 4) return pick_insert_b4(d.policy, d.ghost != 0);
+  if (d.B == 8) return pick_insert_b8(d.policy, d.ghost != 0);
   return nullptr;
 }
 
@@ -269,20 +197,12 @@ void* ck_internal_swap_last(ck_table* t, void* s) {
 int ck_internal_launch_insert(const DevTable& dt, uint32_t block, int sm_count, const uint32_t* keys,
                               const uint32_t* vals, uint64_t n, uint8_t* status, cudaStream_t s,
                               uint64_t max_threads) {
-  cudaError_t e = cudaErrorInvalidValue;
-  bool g = dt.ghost != 0;
-  if (dt.B == 4) {
-    if (dt.policy == CK_QUEUE) e = g ? launch_insert_dt<4, P_QUEUE, true>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s, max_threads)
-                                     : launch_insert_dt<4, P_QUEUE, false>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s, max_threads);
-    else if (dt.policy == CK_RANDOM) e = g ? launch_insert_dt<4, P_RANDOM, true>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s, max_threads)
-                                           : launch_insert_dt<4, P_RANDOM, false>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s, max_threads);
-  } else if (dt.B == 8) {
-    if (dt.policy == CK_QUEUE) e = g ? launch_insert_dt<8, P_QUEUE, true>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s, max_threads)
-                                     : launch_insert_dt<8, P_QUEUE, false>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s, max_threads);
-    else if (dt.policy == CK_RANDOM) e = g ? launch_insert_dt<8, P_RANDOM, true>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s, max_threads)
-                                           : launch_insert_dt<8, P_RANDOM, false>(dt, block, sm_count, true, 0, keys, vals, n, status, nullptr, false, s, max_threads);
-  }
-  return e == cudaSuccess ? CK_OK : CK_ECUDA;
+  if (dt.policy != CK_QUEUE && dt.policy != CK_RANDOM) return CK_ENOTSUP;
+  InsertFn fn = dt.B == 4 ? pick_insert_b4(dt.policy, dt.ghost != 0)
+                          : dt.B == 8 ? pick_insert_b8(dt.policy, dt.ghost != 0) : nullptr;
+  if (!fn) return CK_ECUDA;
+  const InsertLaunch l{&dt, block, sm_count, true, 0, max_threads};
+  return fn(l, keys, vals, n, status, nullptr, false, 0u, s) == cudaSuccess ? CK_OK : CK_ECUDA;
 }
 
 extern "C" {
@@ -398,7 +318,8 @@ int ck_insert_batch_ex(ck_table* t, const uint32_t* d_keys, const uint32_t* d_va
   if (flags & ~(uint32_t)(CK_INS_SERIAL | CK_INS_UPSERT)) return CK_EINVAL;
   InsertFn fn = pick_insert(t);
   if (!fn) return CK_ENOTSUP;
-  cudaError_t e = fn(t, d_keys, d_vals, n, d_status, d_viewed, (flags & CK_INS_SERIAL) != 0,
+  const InsertLaunch l{&t->dt, t->block, t->sm_count, t->overlap != 0, t->load_base, ~0ull};
+  cudaError_t e = fn(l, d_keys, d_vals, n, d_status, d_viewed, (flags & CK_INS_SERIAL) != 0,
                      (flags & CK_INS_UPSERT) ? 1u : 0u, S(stream));
   t->last = S(stream);
   t->load_base += n;
