@@ -67,7 +67,8 @@ extern "C" {
 #define CK_PARAM_MAX_RETRIES 2   /* claim-conflict retries per key; default 64 */
 #define CK_PARAM_RNG_SEED 3      /* seed of the counter-based kick-out draws */
 #define CK_PARAM_HASH_SEED0 10   /* + i for seed_i, i < d (defaults 0x9E3779B9, 0x85EBCA6B, 0xC2B2AE35, 0x27D4EB2F) */
-#define CK_PARAM_BLOCK 20        /* threads per block of the insert kernels */
+#define CK_PARAM_BLOCK 20        /* threads per block of the insert kernels: 32, 64, 128 or 256;
+                                    default 256 for 4-slot queue-kicking tables, else 128 */
 #define CK_PARAM_RATTLE_TIE_RESIDENT 30 /* 1: the resident wins rattle ties (debug reading) */
 #define CK_PARAM_ORDERED_WRITES 31      /* chains are always written back to front (Sec. 8);
                                            1: a release fence between consecutive writes makes
