@@ -45,7 +45,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
     tmp = _LIB + ".tmp%d" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC",
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC", "-pthread",
                            "-o", tmp, _SRC])
     os.replace(tmp, _LIB)
     return _LIB
@@ -69,6 +69,10 @@ def lib():
         L.orc_insert_batch.argtypes = [ctypes.c_void_p, u32p, u32p, ctypes.c_uint64, u8p, u32p, u32p]
         L.orc_lookup_batch.argtypes = [ctypes.c_void_p, u32p, ctypes.c_uint64, u32p, u8p]
         L.orc_delete_batch.argtypes = [ctypes.c_void_p, u32p, ctypes.c_uint64, u8p]
+        L.orc_lookup_batch_threads.argtypes = [ctypes.c_void_p, u32p, ctypes.c_uint64, u32p, u8p, ctypes.c_uint32]
+        L.orc_lookup_batch_threads.restype = ctypes.c_int
+        L.orc_delete_batch_threads.argtypes = [ctypes.c_void_p, u32p, ctypes.c_uint64, u8p, ctypes.c_uint32]
+        L.orc_delete_batch_threads.restype = ctypes.c_int
         L.orc_upsert_batch.argtypes = [ctypes.c_void_p, u32p, u32p, ctypes.c_uint64, u8p]
         L.orc_stats.argtypes = [ctypes.c_void_p, u64p]
         L.orc_n_stats.restype = ctypes.c_uint32
@@ -192,6 +196,25 @@ class OracleTable:
         lib().orc_delete_batch(self._h, _ptr(keys, ctypes.c_uint32), len(keys),
                                _ptr(found, ctypes.c_uint8))
         return found
+
+    def lookup_threads(self, keys, threads):
+        """lookup() split over `threads` host threads; returns (vals, found,
+        threads actually used)."""
+        keys = np.ascontiguousarray(keys, dtype=np.uint32)
+        vals = np.zeros(len(keys), dtype=np.uint32)
+        found = np.zeros(len(keys), dtype=np.uint8)
+        used = lib().orc_lookup_batch_threads(self._h, _ptr(keys, ctypes.c_uint32), len(keys),
+                                              _ptr(vals, ctypes.c_uint32), _ptr(found, ctypes.c_uint8), threads)
+        return vals, found, used
+
+    def delete_threads(self, keys, threads):
+        """delete() of distinct keys split over `threads` host threads;
+        returns (found, threads actually used)."""
+        keys = np.ascontiguousarray(keys, dtype=np.uint32)
+        found = np.zeros(len(keys), dtype=np.uint8)
+        used = lib().orc_delete_batch_threads(self._h, _ptr(keys, ctypes.c_uint32), len(keys),
+                                              _ptr(found, ctypes.c_uint8), threads)
+        return found, used
 
     def upsert(self, keys, vals):
         """Insert, or overwrite the value of a present key (status 5)."""

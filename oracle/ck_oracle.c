@@ -31,6 +31,7 @@
  * mathematics (brute-force matching, invariants, published hash and
  * generator test vectors, hand-worked fixtures); none is left unpinned.
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -430,14 +431,6 @@ static int first_dup_from(const orc_table *t, uint64_t bin, uint32_t start) {
   return -1;
 }
 
-static int first_unclaimed_from(const orc_table *t, uint64_t bin, uint32_t start) {
-  for (uint32_t i = 0; i < t->B; i++) {
-    uint32_t s = (start + i) % t->B;
-    if (!t->claimed[bin * t->B + s]) return (int)s;
-  }
-  return -1;
-}
-
 /* Overwrite the duplicate at `slot` with `rec` and clear the duplicate mark
  * of its twin (Sec. 4: removing one copy leaves the other as a plain
  * record).  Unmarking the twin is a metadata write, not a bin view. */
@@ -549,8 +542,10 @@ static int insert_random2(orc_table *t, uint64_t krec, const uint64_t *b) {
  * free slot the record takes the lowest free slot (in insert-only tables
  * the bin fills in slot order, so this is slot h mod B itself; after
  * deletes a free slot wins over kicking); with ghosts a duplicate, searched from
- * h mod B, is overwritten before any plain record is kicked; a slot the
- * chain already wrote is skipped.  The new key views both bins and takes
+ * h mod B, is overwritten before any plain record is kicked; a walk that
+ * comes back to a bin kicks out the record at h mod B even if this chain
+ * placed it there (the walk has no memory of its path; only the cap ends
+ * it).  The new key views both bins and takes
  * the less full one (load balancing, Sec. 2), b0 on ties; when both are
  * full it takes the one with the smaller hit counter (hit balancing), b0 on
  * ties.  With ghosts, room in both bins gives a ghost pair. */
@@ -576,8 +571,11 @@ static int insert_queue(orc_table *t, uint64_t krec, const uint64_t *b) {
     int s = lowest_free(t, x);
     if (s >= 0) { prop41_check(t, x); put(t, x * t->B + s, cur, 0, 0); return ORC_OK; }
     if (t->ghost && (s = first_dup_from(t, x, h)) >= 0) { prop41_check(t, x); evict_dup(t, x, s, cur); return ORC_OK; }
-    s = first_unclaimed_from(t, x, h);
-    if (s < 0) return ORC_FAILED;
+    /* the record at slot h mod B, whoever placed it: a walk that comes
+     * back to a bin displaces the next record in the bin's queue, which
+     * may be one this chain put there (the walk keeps no memory of its
+     * path; the hit counter has moved on since its last visit) */
+    s = (int)h;
     if (t->cur_kicks == t->cap) return ORC_FAILED;
     cur = kick(t, x, (uint32_t)s, cur);
     x = other_bin(t, cur, x);
@@ -922,54 +920,148 @@ void orc_insert_batch(orc_table *t, const uint32_t *keys, const uint32_t *vals, 
   }
 }
 
-/* Lookup (Sec. 1: a present key is in one of its d bins). */
+/* Lookup of one key (Sec. 1: a present key is in one of its d bins).
+ * Returns 1 and the value if found.  Reads the table only. */
+static int lookup_one(const orc_table *t, uint32_t key, uint32_t *val) {
+  uint64_t b[4];
+  *val = 0;
+  if (key == ORC_RESERVED_KEY) return 0;
+  bins_of(t, key, b);
+  for (uint32_t j = 0; j < t->d; j++)
+    for (uint32_t s = 0; s < t->B; s++) {
+      uint64_t r = t->rec[b[j] * t->B + s];
+      if (r != ORC_EMPTY && key_of(r) == key) { *val = (uint32_t)r; return 1; }
+    }
+  return 0;
+}
+
+/* Delete of one key (Sec. 1): every copy goes; a ghost pair loses both.
+ * Returns found (bit 0) and whether the key was a ghost pair (bit 1).
+ * Writes only the slots holding the key. */
+static int delete_one(orc_table *t, uint32_t key) {
+  uint64_t b[4];
+  int f = 0, was_ghost = 0;
+  if (key == ORC_RESERVED_KEY) return 0;
+  bins_of(t, key, b);
+  for (uint32_t j = 0; j < t->d; j++)
+    for (uint32_t s = 0; s < t->B; s++) {
+      uint64_t slot = b[j] * t->B + s;
+      if (t->rec[slot] != ORC_EMPTY && key_of(t->rec[slot]) == key) {
+        if (t->dup[slot]) was_ghost = 1;
+        t->rec[slot] = ORC_EMPTY;
+        t->dup[slot] = 0;
+        t->rattle[slot] = 0;
+        f = 1;
+      }
+    }
+  return f | (was_ghost << 1);
+}
+
 void orc_lookup_batch(orc_table *t, const uint32_t *keys, uint64_t n, uint32_t *vals, uint8_t *found) {
   for (uint64_t i = 0; i < n; i++) {
-    uint64_t b[4];
-    int f = 0;
-    uint32_t v = 0;
-    if (keys[i] != ORC_RESERVED_KEY) {
-      bins_of(t, keys[i], b);
-      for (uint32_t j = 0; j < t->d && !f; j++)
-        for (uint32_t s = 0; s < t->B && !f; s++) {
-          uint64_t r = t->rec[b[j] * t->B + s];
-          if (r != ORC_EMPTY && key_of(r) == keys[i]) { f = 1; v = (uint32_t)r; }
-        }
-    }
+    uint32_t v;
+    int f = lookup_one(t, keys[i], &v);
     t->stats[OS_LOOKUPS]++;
     t->stats[OS_LOOKUP_HITS] += f;
-    if (vals) vals[i] = f ? v : 0;
+    if (vals) vals[i] = v;
     if (found) found[i] = (uint8_t)f;
   }
 }
 
-/* Delete (Sec. 1): remove every copy of the key; a ghost pair loses both. */
 void orc_delete_batch(orc_table *t, const uint32_t *keys, uint64_t n, uint8_t *found) {
   for (uint64_t i = 0; i < n; i++) {
-    uint64_t b[4];
-    int f = 0, was_ghost = 0;
-    if (keys[i] != ORC_RESERVED_KEY) {
-      bins_of(t, keys[i], b);
-      for (uint32_t j = 0; j < t->d; j++)
-        for (uint32_t s = 0; s < t->B; s++) {
-          uint64_t slot = b[j] * t->B + s;
-          if (t->rec[slot] != ORC_EMPTY && key_of(t->rec[slot]) == keys[i]) {
-            if (t->dup[slot]) was_ghost = 1;
-            t->rec[slot] = ORC_EMPTY;
-            t->dup[slot] = 0;
-            t->rattle[slot] = 0;
-            f = 1;
-          }
-        }
-    }
+    int r = delete_one(t, keys[i]);
     t->stats[OS_DELETES]++;
-    if (f) {
+    if (r & 1) {
       t->stats[OS_DELETE_HITS]++;
       t->stats[OS_SIZE]--;
-      if (was_ghost) t->stats[OS_LIVE_GHOSTS]--;
+      if (r & 2) t->stats[OS_LIVE_GHOSTS]--;
     }
-    if (found) found[i] = (uint8_t)f;
+    if (found) found[i] = (uint8_t)(r & 1);
   }
+}
+
+/* The same lookups and deletes split over `threads` host threads, one
+ * contiguous range of the batch each (the CPU baseline on all cores).
+ * Lookups only read the table.  Deletes of distinct keys write disjoint
+ * slots (every copy of a key lives in that key's own bins), so the ranges
+ * never write the same slot; the keys must be distinct.  Each thread keeps
+ * its own counts, added to the table's counters after the join. */
+typedef struct {
+  orc_table *t;
+  const uint32_t *keys;
+  uint64_t lo, hi;
+  uint32_t *vals;
+  uint8_t *found;
+  int del;
+  uint64_t hits, ghosts;
+} range_job;
+
+static void *range_worker(void *arg) {
+  range_job *j = (range_job *)arg;
+  for (uint64_t i = j->lo; i < j->hi; i++) {
+    if (j->del) {
+      int r = delete_one(j->t, j->keys[i]);
+      j->hits += (uint64_t)(r & 1);
+      j->ghosts += (uint64_t)((r >> 1) & 1);
+      if (j->found) j->found[i] = (uint8_t)(r & 1);
+    } else {
+      uint32_t v;
+      int f = lookup_one(j->t, j->keys[i], &v);
+      j->hits += (uint64_t)f;
+      if (j->vals) j->vals[i] = v;
+      if (j->found) j->found[i] = (uint8_t)f;
+    }
+  }
+  return NULL;
+}
+
+static int run_ranges(orc_table *t, const uint32_t *keys, uint64_t n, uint32_t *vals, uint8_t *found, int del,
+                      uint32_t threads) {
+  if (threads < 1) threads = 1;
+  if (threads > 256) threads = 256;
+  range_job jobs[256];
+  pthread_t tid[256];
+  uint32_t started = 0;
+  for (uint32_t k = 0; k < threads; k++) {
+    range_job *j = &jobs[k];
+    j->t = t;
+    j->keys = keys;
+    j->lo = n * k / threads;
+    j->hi = n * (k + 1) / threads;
+    j->vals = vals;
+    j->found = found;
+    j->del = del;
+    j->hits = j->ghosts = 0;
+  }
+  for (uint32_t k = 1; k < threads; k++) {
+    if (pthread_create(&tid[k], NULL, range_worker, &jobs[k]) != 0) break;
+    started = k;
+  }
+  range_worker(&jobs[0]);
+  for (uint32_t k = 1; k <= started; k++) pthread_join(tid[k], NULL);
+  for (uint32_t k = started + 1; k < threads; k++) range_worker(&jobs[k]);  /* threads that did not start */
+  uint64_t hits = 0, ghosts = 0;
+  for (uint32_t k = 0; k < threads; k++) { hits += jobs[k].hits; ghosts += jobs[k].ghosts; }
+  if (del) {
+    t->stats[OS_DELETES] += n;
+    t->stats[OS_DELETE_HITS] += hits;
+    t->stats[OS_SIZE] -= hits;
+    t->stats[OS_LIVE_GHOSTS] -= ghosts;
+  } else {
+    t->stats[OS_LOOKUPS] += n;
+    t->stats[OS_LOOKUP_HITS] += hits;
+  }
+  return (int)(started + 1);
+}
+
+int orc_lookup_batch_threads(orc_table *t, const uint32_t *keys, uint64_t n, uint32_t *vals, uint8_t *found,
+                             uint32_t threads) {
+  return run_ranges(t, keys, n, vals, found, 0, threads);
+}
+
+int orc_delete_batch_threads(orc_table *t, const uint32_t *keys, uint64_t n, uint8_t *found, uint32_t threads) {
+  return run_ranges(t, keys, n, NULL, found, 1, threads);
 }
 
 /* Insert with the absent-key assumption of Sec. 3 lifted (upsert): a key

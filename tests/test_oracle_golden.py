@@ -1,7 +1,13 @@
 """Hand-worked fixtures (tests/golden/*.txt) pin the oracle's policies step
 by step: each fixture cites the paper section whose definition it works
 through, gives every key's bins explicitly and states the expected status,
-bins viewed, kick-outs and final table state."""
+bins viewed, kick-outs and final table state.
+
+Policies that draw random numbers state the draws a step uses as premises
+(`draw key=K i=I mod M = R`: draw I of key K's insertion, reduced mod M, is
+R).  Each premise is checked against SplitMix64, the generator the draws
+come from (pinned to its published outputs in test_oracle_hash.py), so the
+hand-worked steps rest on the stated residues alone."""
 import glob
 import os
 
@@ -29,7 +35,8 @@ def parse(path):
             for p in kv["policy"].split("|"):
                 pol |= POLICIES[p]
             table = dict(bins=int(kv["bins"]), B=int(kv["B"]), d=int(kv["d"]), policy=pol,
-                         cap=int(kv["cap"]), spawn_k=int(kv.get("spawn_k", 1)))
+                         cap=int(kv["cap"]), spawn_k=int(kv.get("spawn_k", 1)),
+                         tie_resident=kv.get("tie", "incoming") == "resident")
         elif head == "insert":
             lhs, rhs = rest.split("->")
             kv = dict(x.split("=") for x in lhs.split())
@@ -38,6 +45,10 @@ def parse(path):
             r = rhs.split()
             exp = dict(x.split("=") for x in r[1:])
             steps.append(("insert", key, val, STATUS[r[0]], int(exp["viewed"]), int(exp["kicks"])))
+        elif head == "draw":  # draw key=K i=I mod M = R: a premise about the draws
+            kv = dict(x.split("=") for x in rest.split("mod")[0].split())
+            mod, res = rest.split("mod")[1].split("=")
+            steps.append(("draw", int(kv["key"]), int(kv["i"]), int(mod), int(res)))
         elif head == "set":  # set spawn <bin> = <count>: a starting state of the fixture
             what, rhs = rest.split("=")
             what = what.split()
@@ -60,8 +71,15 @@ def test_golden(path):
     keys = sorted(keybins)
     t.set_bins(np.array(keys, dtype=np.uint32), np.array([keybins[k] for k in keys], dtype=np.uint64))
     t.set_spawn_k(table["spawn_k"])
+    if table["tie_resident"]:
+        t.set_rattle_tie_resident(True)
     for step in steps:
-        if step[0] == "insert":
+        if step[0] == "draw":
+            # the fixture table's draw seed is 0: draw i of key k is the
+            # SplitMix64 output for state k ^ (i << 32)
+            _, key, i, mod, res = step
+            assert oracle.lib().orc_splitmix64_at(key ^ (i << 32)) % mod == res, (path, step)
+        elif step[0] == "insert":
             _, key, val, st, viewed, kicks = step
             s, v, k = t.insert([key], [val], trace=True)
             assert (int(s[0]), int(v[0]), int(k[0])) == (st, viewed, kicks), (path, key)
@@ -87,6 +105,8 @@ def test_golden(path):
                 b = int(what[1])
                 got = ",".join(str(int(x)) for x in e["dup"][b * t.B:(b + 1) * t.B])
                 assert got == rhs, (path, what)
+            elif what[0] == "rattle":
+                assert int(e["rattle"][int(what[1])]) == int(rhs), (path, what)
             elif what[0] in ("hit", "spawn"):
                 assert int(e[what[0]][int(what[1])]) == int(rhs), (path, what)
             elif what[0] == "stat":

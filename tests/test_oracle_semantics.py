@@ -177,3 +177,29 @@ def test_upsert_against_a_dict(d, B, policy):
         recs = e["rec"][e["dup"] == 1]
         for r in recs:
             assert (int(r) & 0xFFFFFFFF) == want[int(r) >> 32]
+
+
+@pytest.mark.parametrize("policy", [oracle.QUEUE, oracle.RANDOM | oracle.GHOST, oracle.RATTLE])
+def test_threaded_lookups_and_deletes_equal_the_serial_ones(policy):
+    """The all-core legs of the CPU baseline split a batch over host
+    threads; every result, the counters and the remaining table equal the
+    one-thread calls."""
+    d, B = (3, 1) if policy == oracle.RATTLE else (2, 4)
+    bins = 1 << 12
+    n = inputs.load_target(bins * B, 0.85)
+    keys, nxt = inputs.distinct_keys(n, 4)
+    vals = inputs.values_for(keys)
+    a = oracle.OracleTable(bins, B, d, policy, rng_seed=1, cap=500)
+    b = oracle.OracleTable(bins, B, d, policy, rng_seed=1, cap=500)
+    a.insert(keys, vals)
+    b.insert(keys, vals)
+    lk, _ = inputs.lookup_keys(keys, 20000, 4, 0.5, next_start=nxt)
+    v1, f1 = a.lookup(lk)
+    v2, f2, used = b.lookup_threads(lk, 5)
+    assert used == 5 and np.array_equal(v1, v2) and np.array_equal(f1, f2)
+    dk = inputs.delete_keys(keys, n // 3, 4)
+    g1 = a.delete(dk)
+    g2, used = b.delete_threads(dk, 5)
+    assert used == 5 and np.array_equal(g1, g2)
+    assert a.stats() == b.stats() and a.contents() == b.contents()
+    assert b.check_invariants()[0] == 0
