@@ -8,10 +8,13 @@ keys; everything through the C ABI (libck.so) on device-resident inputs.
 The table (512 MiB) and key arrays are larger than L2, so no flush is needed
 between steps.
 
-Prints one JSON line (rank 0).  `value` is M inserts/s over the fills;
-lookups/s, deletes/s, bins viewed per insertion, per-policy fills, the
-roofline of the dominant kernel, the end-to-end number through host buffers
-and the oracle's CPU baseline ride along.
+Rank 0 prints the side sections first, one JSON line each with a
+"section" key (per-policy fills, the batched and serving forms, the
+transactional layer, L2-resident small table, probe sweeps), then the bench
+line last: one compact JSON line whose `value` is M inserts/s over the
+fills, with lookups/s, deletes/s, bins viewed per insertion, the roofline of
+the dominant kernel, the end-to-end number through host buffers and the
+oracle's CPU baseline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -252,6 +255,25 @@ def viewed_curve(t, points=(0.5, 0.7, 0.8, 0.9, 0.95)):
     return out
 
 
+def contents_exact(torch, t, kt, vt, st, stream):
+    """The table's key -> value map after a fill is exactly the keys whose
+    insertion returned OK, with their values: every such key is found with
+    its value, every key reported FAILED is absent, no status other than OK
+    or FAILED occurs, and the table's size counter equals the OK count."""
+    n = kt.numel()
+    v = torch.empty(n, dtype=torch.int32, device="cuda")
+    f = torch.empty(n, dtype=torch.uint8, device="cuda")
+    t.lookup(kt, v, f, stream)
+    torch.cuda.synchronize()
+    okm = st == 0
+    good = bool(((st == 0) | (st == 1)).all().item())
+    good &= bool(torch.equal(f.bool(), okm))
+    good &= bool(torch.equal(v[okm], vt.view(torch.int32)[okm]))
+    good &= int(t.stats()["size"]) == int(okm.sum().item())
+    del v, f
+    return good
+
+
 def policy_fills(torch, ck, stream, base_keys):
     """One fill per policy on the same shapes (the policy rows of the path)."""
     from paper_1605_05236_gb300 import inputs
@@ -272,7 +294,9 @@ def policy_fills(torch, ck, stream, base_keys):
         fill_once(torch, ck, t, kt, vt, st, stream)  # warm
         ms, _ = fill_once(torch, ck, t, kt, vt, st, stream)
         s = t.stats()
+        exact = contents_exact(torch, t, kt, vt, st, stream)
         out[name] = {"table": "2^24x4", "load": LOAD, "m_inserts_per_s": round(len(keys) / ms / 1e3, 2),
+                     "contents_exact": exact,
                      "bins_viewed_per_insert": round(s["bins_viewed_per_insert"], 4),
                      "viewed_by_load": viewed_curve(t),
                      "kicks_per_insert": round(s["kicks"] / max(1, s["inserts_ok"]), 4),
@@ -311,7 +335,7 @@ def policy_fills(torch, ck, stream, base_keys):
         ms, _ = fill_once(torch, ck, t, kt, vt, st, stream)
         s = t.stats()
         rec = {"table": "2^%dx%d d=%d" % (int(np.log2(bins)), b, d), "load": load, "cap": cap,
-               "hash_family": family,
+               "hash_family": family, "contents_exact": contents_exact(torch, t, kt, vt, st, stream),
                "m_inserts_per_s": round(n / ms / 1e3, 2),
                "bins_viewed_per_insert": round(s["bins_viewed_per_insert"], 4),
                "viewed_by_load": viewed_curve(t, tuple(q for q in (0.5, 0.7, 0.8, 0.9, 0.95, 0.96, 0.97, 0.99)
@@ -619,11 +643,13 @@ def host_info():
 
 
 def cpu_baseline():
-    """The oracle, as it stands, on one host core: a bounded sample of the
+    """The oracle, as it stands, on the host cores: a bounded sample of the
     workload (a 2^22-bin x 4-slot table filled to 0.95 with queue-kicking,
     then 2^22 lookups at 50% hits and 2^20 deletes of present keys).  The
-    oracle is serial (its batch calls keep counters), so every leg uses one
-    core."""
+    fill is serial (the policies are defined one insertion at a time), so it
+    runs on one core; the lookups and deletes run on one core and again on
+    all cores (the batch split into one range per core, on a second copy of
+    the filled table)."""
     import oracle
     from paper_1605_05236_gb300 import inputs
     bins = 1 << 22
@@ -643,11 +669,25 @@ def cpu_baseline():
     t0 = time.perf_counter()
     t.delete(dk)
     dd = time.perf_counter() - t0
+    # all cores: a second table filled the same way (the serial fill is
+    # deterministic), its lookups and deletes split over every core
+    cores = os.cpu_count() or 1
+    t2 = oracle.OracleTable(bins, B, 2, oracle.QUEUE, rng_seed=1, cap=500)
+    t2.insert(keys, vals)
+    t0 = time.perf_counter()
+    _, _, used_l = t2.lookup_threads(lk, cores)
+    dl_all = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, used_d = t2.delete_threads(dk, cores)
+    dd_all = time.perf_counter() - t0
     return {"value": round(n / dt / 1e6, 3), "unit": "M inserts/s", "cores": 1, "kind": "oracle",
             "sample": "serial C oracle, queue-kicking fill of a 2^22-bin x 4-slot table from empty to 0.95 "
-                      "(%d keys, %.1f s); bins viewed/insert %.4f; then %d lookups (50%% hits) and %d deletes "
-                      "of present keys on the filled table" % (n, dt, s["bins_viewed"] / n, len(lk), len(dk)),
+                      "(%d keys, %.1f s, 1 core); bins viewed/insert %.4f; then %d lookups (50%% hits) and %d "
+                      "deletes of present keys on the filled table, on 1 core and on all %d cores"
+                      % (n, dt, s["bins_viewed"] / n, len(lk), len(dk), cores),
             "m_lookups_per_s": round(len(lk) / dl / 1e6, 3), "m_deletes_per_s": round(len(dk) / dd / 1e6, 3),
+            "all_cores": {"cores": min(used_l, used_d), "m_lookups_per_s": round(len(lk) / dl_all / 1e6, 3),
+                          "m_deletes_per_s": round(len(dk) / dd_all / 1e6, 3)},
             "host": host_info()}
 
 
@@ -819,21 +859,39 @@ def run_gpu(args, rank, world, local):
            "ms": {"fill": round(fill_ms / K, 3), "lookup": round(look_ms / K, 3), "delete": round(del_ms / K, 3)},
            "exact": {"all_inserted": ok, "lookups": lookups_exact, "lookup_values": vals_exact,
                      "deletes": deletes_exact},
-           "roofline": roofline, "roofline_lookup": roof_lookup, "insert_batches": profile,
+           "roofline": roofline, "roofline_lookup": roof_lookup,
            "e2e": e2e, "gpu_launches": launches_per_step * K, "clocks": clk}
+    sections = {"insert_batches": profile, "roofline_detail": {"insert": roofline, "lookup": roof_lookup},
+                "e2e_detail": e2e}
     del kt, vt, lkt, dkt, st, lv, lf, df
     table.close()
     torch.cuda.empty_cache()
+    summary = {}
     if rank == 0 and world == 1 and not args.no_policies:
-        out["policies"] = policy_fills(torch, ck, stream, (keys, vals))
+        pol = policy_fills(torch, ck, stream, (keys, vals))
+        sections["policies"] = pol
+        summary["policies"] = {
+            "queue_vs_random_bins_viewed": [pol["queue"]["bins_viewed_per_insert"],
+                                            pol["random"]["bins_viewed_per_insert"]],
+            "failed_total": sum(int(p.get("failed", 0)) for p in pol.values()),
+            "contents_exact": all(p.get("contents_exact", True) for p in pol.values())}
     if rank == 0 and world == 1 and not args.no_multi:
-        out["batched_form"] = multi_form(torch, ck, stream)
+        mf = multi_form(torch, ck, stream)
+        sections["batched_form"] = mf
+        summary["batched_form"] = {"speedup_vs_per_table": mf["speedup"],
+                                   "m_inserts_per_s": mf["batched"]["m_inserts_per_s"],
+                                   "all_inserted": mf["batched"]["all_inserted"] and mf["per_table"]["all_inserted"]}
     if rank == 0 and world == 1 and not args.no_serve:
-        out["serving_form"] = serve_form(torch, ck, stream)
+        sf = serve_form(torch, ck, stream)
+        sections["serving_form"] = sf
+        summary["serving_form"] = {k: {"results_exact": v["results_exact"], "speedup": v["throughput_speedup"]}
+                                   for k, v in sf.items() if k.startswith("mix_")}
     if rank == 0 and world == 1 and not args.no_txn:
-        out["transactional"] = txn_form(torch, stream)
+        sections["transactional"] = txn_form(torch, stream)
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline()
+    out["sections"] = sections
+    out["section_summary"] = summary
     if world > 1:
         torch.distributed.destroy_process_group()
     return out
@@ -1023,17 +1081,68 @@ def run_section(name):
     return {"policies": policy_fills(torch, ck, stream, (keys, vals))}
 
 
+def headline(out):
+    """The bench line proper: the contract's keys and the headline figures,
+    compact (well under 4 KB) so it can be read alone as the last line of
+    the output.  The side sections go out on earlier lines."""
+    keep = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+            "vs_baseline", "dtype", "data", "config", "bins_viewed_per_insert", "kicks_per_insert",
+            "claim_aborts_per_insert", "m_lookups_per_s", "m_deletes_per_s", "ms", "exact", "gpu_launches",
+            "clocks")
+    h = {k: out[k] for k in keep if k in out}
+    r = out.get("roofline")
+    if r:
+        h["roofline"] = {k: r[k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac", "traffic",
+                                           "bytes_per_launch", "avg_launch_ms") if k in r}
+        h["roofline"]["peak_kind"] = r.get("peak_kind", "").split(" ")[0]
+        if "vs_random_gather_32B" in r:
+            h["roofline"]["vs_random_gather_32B"] = r["vs_random_gather_32B"]
+        if "random_ops_model" in r:
+            h["roofline"]["random_ops_model_frac"] = r["random_ops_model"]["frac"]
+    rl = out.get("roofline_lookup")
+    if rl:
+        h["roofline_lookup"] = {k: rl[k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac",
+                                                   "vs_random_gather_32B") if k in rl}
+    e = out.get("e2e")
+    if e:
+        h["e2e"] = {k: e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step", "ms_per_step",
+                                      "results_exact") if k in e}
+        if "whole_step" in e:
+            h["e2e"]["whole_step_value"] = e["whole_step"]["value"]
+    cb = out.get("cpu_baseline")
+    if cb:
+        h["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "m_lookups_per_s",
+                                                "m_deletes_per_s", "all_cores") if k in cb}
+        host = cb.get("host") or {}
+        h["cpu_baseline"]["host"] = {"nproc": host.get("nproc"), "machine": host.get("machine")}
+    h["sections"] = out.get("section_summary", {})
+    line = json.dumps(h)
+    # the side summaries are the first thing to go should the line grow
+    if len(line) > 3800:
+        h["sections"] = {"note": "see the section lines above"}
+        line = json.dumps(h)
+    return line
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         out = run_reference(args, rank, world)
-    elif args.only:
+        if rank == 0 and out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if args.only:
         out = run_section(args.only)
-    else:
-        out = run_gpu(args, rank, world, local)
+        if rank == 0 and out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    out = run_gpu(args, rank, world, local)
     if rank == 0 and out is not None:
-        print(json.dumps(out), flush=True)
+        # side sections first, one line each; the bench line last
+        for name, body in out.get("sections", {}).items():
+            print(json.dumps({"section": name, **body}), flush=True)
+        print(headline(out), flush=True)
 
 
 if __name__ == "__main__":
