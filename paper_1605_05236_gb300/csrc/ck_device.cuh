@@ -11,14 +11,17 @@
 //       28-31 version;  d-ary: bit 0 claim flag, bits 8-15 rattle counter of
 //       the resident key (Sec. 7), 28-31 version.
 //
-// Every write to a slot happens while its claim flag is held.  A claim is a
-// compare-and-swap of the whole metadata word from the value read when the
-// bin was viewed, so a successful claim also proves that nothing in the bin
-// changed since the view: every release adds one to the version field (the
-// release also folds in the duplicate/rattle update of the slot), and the
-// hit counter of queue-kicking moves on every insertion.  The metadata word
-// is read with acquire semantics before the slots, so the slots seen are at
-// least as new as that word.
+// Every write to an occupied slot happens while its claim flag is held.  A
+// claim is a compare-and-swap of the whole metadata word from the value read
+// when the bin was viewed, so a successful claim also shows that nothing in
+// the bin changed since the view -- every release adds one to the version
+// field (the release also folds in the duplicate/rattle update of the slot),
+// and the hit counter of queue-kicking moves on every insertion -- unless
+// the word came back to the value seen (the 4-bit version wraps after 16
+// releases).  The writes themselves are therefore 64-bit compare-and-swaps
+// from the records the plan saw, undone if one fails, which closes that
+// gap.  The metadata word is read with acquire semantics before the slots,
+// so the slots seen are at least as new as that word.
 #pragma once
 #include <cstdint>
 #include <cuda/atomic>
@@ -249,6 +252,13 @@ __device__ __forceinline__ uint32_t add_release(uint32_t* p, uint32_t delta) {
 // 64-bit compare-and-swap of one slot (relaxed): the unclaimed placement
 // of a new key into a free slot, and a chain's write of its terminal free
 // slot, both of which must not overwrite a key another thread placed there.
+__device__ __forceinline__ uint64_t cas_slot_old(uint64_t* p, uint64_t expected, uint64_t desired) {
+  unsigned long long old;
+  asm volatile("atom.relaxed.gpu.global.cas.b64 %0, [%1], %2, %3;"
+               : "=l"(old) : "l"(p), "l"(expected), "l"(desired) : "memory");
+  return old;
+}
+
 __device__ __forceinline__ bool cas_slot(uint64_t* p, uint64_t expected, uint64_t desired) {
   unsigned long long old;
   asm volatile("atom.relaxed.gpu.global.cas.b64 %0, [%1], %2, %3;"

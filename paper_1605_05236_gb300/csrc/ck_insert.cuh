@@ -24,11 +24,16 @@ namespace ck {
 
 enum Kind : uint8_t { K_MOVE = 0, K_DUPTERM = 1, K_TWIN = 2, K_GHOST = 3 };
 
-// A plan: one 16-byte entry per claimed slot, stored as two 64-bit words:
-// a packed descriptor -- bits 0-31 bin, 32-34 slot, 35-36 kind, 37
-// hit-counter increment, 40-47 rattle counter of the displaced key, 48-55
-// rattle counter of the incoming key -- and the record the slot held when it
-// was claimed.  Beyond the first REG_ENTRIES (registers), entries live in
+// A plan: one 16-byte entry per chain step or claimed slot, stored as two
+// 64-bit words: a packed descriptor -- bits 0-31 bin, 32-34 slot, 35-36
+// kind, 37 hit-counter increment, 38 revisit, 39 superseded; single-slot
+// bins: 40-47 rattle counter of the displaced key, 48-55 rattle counter of
+// the incoming key; bucketized bins: 40-55 the previous entry of a revisit
+// -- and the record the slot held when the step was planned.  A revisit is
+// a queue-kicking step into a slot the plan already holds (the walk came
+// back to a bin): it takes no claim of its own, its record is the one the
+// plan placed there, and the earlier entry for that slot is marked
+// superseded (its write is replaced by the revisit's).  Beyond the first REG_ENTRIES (registers), entries live in
 // local memory (MAX_CHAIN of them, the concurrent kernel) or in table
 // scratch (LONG_CHAIN: the serial replay and chains longer than MAX_CHAIN).
 template <int N>
@@ -47,6 +52,11 @@ __device__ __forceinline__ uint32_t e_kind(uint64_t e) { return (uint32_t)(e >> 
 __device__ __forceinline__ bool e_hit(uint64_t e) { return (e >> 37) & 1u; }
 __device__ __forceinline__ uint32_t e_old_r(uint64_t e) { return (uint32_t)(e >> 40) & 255u; }
 __device__ __forceinline__ uint32_t e_new_r(uint64_t e) { return (uint32_t)(e >> 48) & 255u; }
+constexpr uint64_t E_REVISIT = 1ull << 38;
+constexpr uint64_t E_SUPERSEDED = 1ull << 39;
+__device__ __forceinline__ bool e_rev(uint64_t e) { return (e & E_REVISIT) != 0; }
+__device__ __forceinline__ bool e_sup(uint64_t e) { return (e & E_SUPERSEDED) != 0; }
+__device__ __forceinline__ int e_prev(uint64_t e) { return (int)((e >> 40) & 0xFFFFu); }
 
 // The first REG_ENTRIES entries of a plan stay in registers (most chains
 // are one or two slots long); the rest go to memory at pe, indexed by entry
@@ -73,6 +83,7 @@ struct Ctx {
   int pn;
   int pcap;
   int long_id;    // scratch plan in use (index in the table's pool), or -1
+  int big_id;     // scratch plan region lent to a search as its larger space, or -1
   uint64_t held;  // d-ary walks: the record in hand
 };
 
@@ -162,6 +173,54 @@ __device__ __forceinline__ bool claim(const DevTable& t, Ctx& c, uint32_t bin, u
   return true;
 }
 
+// The record in slot s of `bin`, read after this insertion claimed the slot.
+// It must be the record the plan saw there: a claim validates its view
+// through the bin's metadata word, which can come back to the value seen (a
+// 4-bit version wraps after 16 releases); once the claim is held the slot
+// cannot change, so this one read settles it.  Walks issue it together with
+// the next step's loads and compare after them.
+template <int B>
+__device__ __forceinline__ uint64_t reread(const DevTable& t, uint32_t bin, uint32_t s) {
+  return ld_slot(t.slots + (uint64_t)bin * B + s);
+}
+
+// Slots of `bin` this plan holds claims on (revisits hold none of their own).
+__device__ __forceinline__ uint32_t own_slots(const Ctx& c, uint32_t bin) {
+  uint32_t m = 0;
+  for (int i = 0; i < c.pn; i++) {
+    uint64_t e = desc_at(c, i);
+    if (e_bin(e) == bin && !e_rev(e)) m |= 1u << e_slot(e);
+  }
+  return m;
+}
+
+// The plan's latest entry for slot s of `bin`, or -1.
+__device__ __forceinline__ int last_entry_for(const Ctx& c, uint32_t bin, uint32_t s) {
+  for (int i = c.pn - 1; i >= 0; i--) {
+    uint64_t e = desc_at(c, i);
+    if (e_bin(e) == bin && e_slot(e) == s) return i;
+  }
+  return -1;
+}
+
+// The record chain entry j receives: the new record, or the record entry
+// j - 1 displaced.
+__device__ __forceinline__ uint64_t placed_by(const Ctx& c, int j) {
+  return j == 0 ? c.krec : content_at(c, j - 1);
+}
+
+// A queue-kicking step into slot s of `bin`, which the plan already holds
+// (entry j placed the record there): the hit counter advances by CAS from
+// the viewed metadata word, which also validates the view, and the new
+// entry takes over entry j's write.
+__device__ __forceinline__ bool claim_again(const DevTable& t, Ctx& c, uint32_t bin, uint32_t m, int s, int j,
+                                            uint64_t victim) {
+  if (!cas_acquire(t.meta + bin, m, m + HIT_ONE)) return false;
+  set_entry(c, j, desc_at(c, j) | E_SUPERSEDED, content_at(c, j));
+  put_entry(c, pack_entry(bin, s, K_MOVE, true, 0, 0) | E_REVISIT | ((uint64_t)j << 40), victim);
+  return true;
+}
+
 // A new key straight into free slot s of `bin` (tables without ghosts):
 // one 64-bit compare-and-swap of the slot from empty to the record, then a
 // relaxed add that advances the bin's version (and, for queue-kicking, its
@@ -176,25 +235,61 @@ __device__ __forceinline__ bool place_direct(const DevTable& t, Ctx& c, uint32_t
   return true;
 }
 
-// Abandon the plan: drop every claim (and hit increment); nothing was written.
-__device__ __forceinline__ void release_all(const DevTable& t, Ctx& c) {
+// Abandon the plan: drop every claim (and hit increment).  Nothing was
+// written, or (bump) every write was undone: then the version moves too, so
+// that a reader validating a miss across the undone writes looks again.
+__device__ __forceinline__ void release_all(const DevTable& t, Ctx& c, bool bump = false) {
   for (int i = 0; i < c.pn; i++) {
     uint64_t e = desc_at(c, i);
-    red_relaxed(t.meta + e_bin(e), 0u - ((1u << e_slot(e)) + (e_hit(e) ? HIT_ONE : 0u)));
+    red_relaxed(t.meta + e_bin(e),
+                (bump ? VER_ONE : 0u) - ((e_rev(e) ? 0u : 1u << e_slot(e)) + (e_hit(e) ? HIT_ONE : 0u)));
   }
   c.pn = 0;
 }
 
-// Apply the plan back to front, then release every claim.  Entry 0 of the
-// chain receives the new record, entry i the record entry i-1 held.  With
-// ordered writes a release fence separates consecutive stores, so a key is
-// never absent for a concurrent reader (Sec. 8); one fence then orders all
-// stores before the relaxed releases, each of which also moves the version,
-// duplicate mark or rattle counter of its slot.
-// The chain's first write, to its terminal, is a compare-and-swap when the
-// terminal is a free slot (a new key may have taken it without a claim); if
-// that fails nothing has been written, and the caller drops the claims and
-// starts again (false).
+// The record `rec` may live in `bin`: it is a record (not an empty slot)
+// and `bin` is one of its key's bins (Sec. 1).
+template <int B>
+__device__ __forceinline__ bool belongs(const DevTable& t, uint64_t rec, uint32_t bin) {
+  if (rec == EMPTY) return false;
+  if constexpr (B == 1) {
+    uint32_t b[4];
+    bins_of(t, key_of(rec), b);
+    bool ok = false;
+    for (uint32_t j = 0; j < t.d; j++) ok |= b[j] == bin;
+    return ok;
+  } else {
+    uint32_t b0, b1;
+    bins2(t, key_of(rec), b0, b1);
+    return bin == b0 || bin == b1;
+  }
+}
+
+// Chain entry i's slot.
+template <int B>
+__device__ __forceinline__ uint64_t* slot_at(const DevTable& t, uint64_t e) {
+  return t.slots + (uint64_t)e_bin(e) * B + e_slot(e);
+}
+
+// Apply the plan back to front, then release every claim (Sec. 8).  Entry 0
+// of the chain receives the new record, entry i the record entry i-1 held.
+//
+// Every slot of the plan was validated when it was claimed: a claim is a
+// compare-and-swap of the bin's metadata word from the value seen when the
+// bin was viewed, and since that word can come back to an earlier value (its
+// version field wraps), the slot itself is read once more after the claim
+// and must still hold the record the plan saw (check_claimed; a search
+// reads its path's records after claiming them and checks that each belongs
+// to the bin it moves into).  A claimed slot holding a record cannot change
+// until its claim is released, so the writes below need no further check --
+// except the chain's terminal, the first write: a free terminal can be taken
+// by a new key without a claim (place_direct), so it is written by a
+// compare-and-swap, and if that fails nothing has been written and the
+// caller abandons the plan (false).  With ordered writes a release fence
+// separates consecutive writes, so a key is never absent for a concurrent
+// reader; one fence then orders all writes before the relaxed releases, each
+// of which also moves the version, duplicate mark or rattle counter of its
+// slot.
 template <int B>
 __device__ __forceinline__ bool commit(const DevTable& t, Ctx& c) {
   if (c.pn == 0) return true;  // placed directly (place_direct)
@@ -202,25 +297,35 @@ __device__ __forceinline__ bool commit(const DevTable& t, Ctx& c) {
   while (n_chain < c.pn && (e_kind(desc_at(c, n_chain)) == K_MOVE || e_kind(desc_at(c, n_chain)) == K_DUPTERM))
     n_chain++;
   for (int i = n_chain - 1; i >= 0; i--) {
-    uint64_t rec = (i == 0) ? c.krec : content_at(c, i - 1);
-    uint64_t ei = desc_at(c, i);
-    uint64_t* p = t.slots + (uint64_t)e_bin(ei) * B + e_slot(ei);
-    if (i == n_chain - 1 && e_kind(ei) == K_MOVE && content_at(c, i) == EMPTY) {
-      if (!cas_slot(p, EMPTY, rec)) return false;
+    const uint64_t e = desc_at(c, i);
+    if (e_sup(e)) continue;  // a later revisit of this slot writes it
+    const uint64_t rec = (i == 0) ? c.krec : content_at(c, i - 1);
+    uint64_t* p = slot_at<B>(t, e);
+    if (i == n_chain - 1) {
+      if (!cas_slot(p, content_at(c, i), rec)) return false;
     } else {
       st_slot(p, rec);
     }
     if (t.ordered_writes && i > 0) fence_release();  // the copy lands before its source is overwritten
   }
+  // ghost pairs (Sec. 4): the new record into both free slots
   for (int i = n_chain; i < c.pn; i++) {
-    uint64_t ei = desc_at(c, i);
-    if (e_kind(ei) == K_GHOST) st_slot(t.slots + (uint64_t)e_bin(ei) * B + e_slot(ei), c.krec);
+    const uint64_t e = desc_at(c, i);
+    if (e_kind(e) != K_GHOST) continue;
+    if (!cas_slot(slot_at<B>(t, e), EMPTY, c.krec)) {
+      for (int j = n_chain; j < i; j++) {
+        const uint64_t f = desc_at(c, j);
+        if (e_kind(f) == K_GHOST) st_slot(slot_at<B>(t, f), EMPTY);
+      }
+      fence_release();
+      return false;
+    }
   }
   fence_release();
   for (int i = 0; i < c.pn; i++) {
     uint64_t ei = desc_at(c, i);
     uint32_t sl = e_slot(ei);
-    uint32_t delta = VER_ONE - (1u << sl);
+    uint32_t delta = VER_ONE - (e_rev(ei) ? 0u : 1u << sl);
     if (B == 1) {
       delta += (e_new_r(ei) - e_old_r(ei)) << RATTLE_SHIFT;
     } else if (e_kind(ei) == K_GHOST) {
@@ -266,7 +371,7 @@ __device__ __forceinline__ bool claim_twin(const DevTable& t, Ctx& c, uint64_t g
     for (int u = 0; u < B; u++)
       if (s < 0 && ((dm >> u) & 1u) && v.s[u] == g) s = u;
     if (s < 0) return false;
-    if (claim(t, c, y, v.m, s, K_TWIN, false, g)) return true;
+    if (claim(t, c, y, v.m, s, K_TWIN, false, g)) return reread<B>(t, y, (uint32_t)s) == g;
   }
   return false;
 }
@@ -386,8 +491,10 @@ __device__ int insert_random2(const DevTable& t, Ctx& c) {
     if (st != ST_OK) return st;
     c.kicks++;
     uint64_t victim = slot_of<B>(vx, s);
+    const uint64_t chk = reread<B>(t, x, (uint32_t)s);
     x = other_bin2(t, victim, x);
     load_view<B>(t, x, vx);
+    if (chk != victim) return ST_CONFLICT;
     c.viewed++;
     uint32_t fm = free_mask<B>(vx);
     if (fm) return take_free<B>(t, c, x, vx, lowest(fm), false);
@@ -411,8 +518,9 @@ __device__ int insert_random2(const DevTable& t, Ctx& c) {
 // claim of a kicked slot and the increment are one compare-and-swap, the GPU
 // form of the paper's fetch-and-add scheduling).  A record goes to the
 // lowest free slot (in insert-only tables the bin fills in slot order, so
-// this is slot h mod B); a full bin gives up its first unclaimed slot from
-// h mod B, the record that has been there longest.
+// this is slot h mod B); a full bin gives up the record at h mod B, the one
+// that has been there longest -- also when this chain placed it there on an
+// earlier visit -- skipping only slots another insertion holds.
 template <int B, bool GHOST>
 __device__ int insert_queue(const DevTable& t, Ctx& c) {
   constexpr uint32_t FULL = (1u << B) - 1;
@@ -479,26 +587,37 @@ __device__ int insert_queue(const DevTable& t, Ctx& c) {
       } else if (GHOST && dup_mask<B>(vx)) {
         return take_dup<B>(t, c, x, vx, first_from<B>(dup_mask<B>(vx), h), true);
       } else {
+        // the victim: the record at slot h mod B, skipping slots another
+        // insertion holds; a slot this chain already wrote is taken again
+        // (the walk came back to the bin; its queue has moved on), with the
+        // record the chain put there
         uint32_t claimed = claimed_mask<B>(vx);
-        uint32_t um = FULL & ~claimed & ~(vx.m >> DUP_SHIFT);
+        uint32_t own = claimed ? own_slots(c, x) : 0u;
+        uint32_t foreign = claimed & ~own;
+        uint32_t um = FULL & ~foreign & ~((vx.m >> DUP_SHIFT) & ~own);
         // a detour around another insertion's claim: reaching the cap after
         // one is not the serial algorithm's failure
-        if (claimed && !c.foreign && !claims_all_ours<B>(c, x, claimed)) c.foreign = 1;
+        if (foreign) c.foreign = 1;
         int s = first_from<B>(um, h);
         if (s < 0) return c.foreign ? ST_CONFLICT : ST_FAILED;
         if (c.kicks == t.cap) return c.foreign ? ST_CONFLICT : ST_FAILED;
         if (int r0 = plan_room(t, c)) return r0;
-        const uint64_t victim = slot_of<B>(vx, s);
+        const bool rev = (own >> s) & 1u;
+        const int jprev = rev ? last_entry_for(c, x, (uint32_t)s) : -1;
+        const uint64_t victim = rev ? placed_by(c, jprev) : slot_of<B>(vx, s);
         const uint32_t xn = other_bin2(t, victim, x);
         // the next bin's metadata word travels with the claim; a fence
         // then orders it before that bin's slots
         const uint32_t mn = ld_relaxed(t.meta + xn);
-        if (claim(t, c, x, vx.m, s, K_MOVE, true, victim)) {
+        if (rev ? claim_again(t, c, x, vx.m, s, jprev, victim) : claim(t, c, x, vx.m, s, K_MOVE, true, victim)) {
           c.kicks++;
+          // a slot the chain holds already carries the plan's record
+          const uint64_t chk = rev ? victim : reread<B>(t, x, (uint32_t)s);
           x = xn;
           vx.m = mn;
           fence_acquire();
           load_slots<B>(t, x, vx);
+          if (chk != victim) return ST_CONFLICT;
           break;
         }
       }
@@ -595,12 +714,14 @@ __device__ inline int insert_random_dary(const DevTable& t, Ctx& c) {
     c.kicks++;
     holder = x;
     c.held = vx.s[0];
+    const uint64_t chk = reread<1>(t, x, 0);
     uint32_t vb[4];
     bins_of(t, key_of(vx.s[0]), vb);
     View<1> w[4];
 #pragma unroll
     for (int i = 0; i < 4; i++)
       if (i < (int)t.d && vb[i] != x) load_view<1>(t, vb[i], w[i]);
+    if (chk != c.held) return ST_CONFLICT;
     nc = 0;
     for (uint32_t i = 0; i < t.d; i++) {
       if (vb[i] == x) continue;  // just claimed by this chain
@@ -619,6 +740,8 @@ __device__ inline int insert_random_dary(const DevTable& t, Ctx& c) {
 __device__ inline int insert_rattle(const DevTable& t, Ctx& c) {
   uint64_t cur = c.krec;
   uint32_t rc = 0;
+  const uint64_t* pend = nullptr;  // the slot the last kick claimed, re-read with the next view (reread)
+  uint64_t pend_v = 0;
   for (uint32_t tries = 0;; tries++) {
     if (tries == t.cap) return c.foreign ? ST_CONFLICT : ST_FAILED;
     if (int r = plan_room(t, c)) return r;
@@ -627,7 +750,12 @@ __device__ inline int insert_rattle(const DevTable& t, Ctx& c) {
     uint32_t x = vb[rc % t.d];
     rc = rc < 255 ? rc + 1 : 255;
     View<1> vx;
+    const uint64_t chk = pend ? ld_slot(pend) : 0;
     load_view<1>(t, x, vx);
+    if (pend) {
+      if (chk != pend_v) return ST_CONFLICT;
+      pend = nullptr;
+    }
     if (claimed_mask<1>(vx)) {
       // this chain's own bin: skipped, not viewed; another insertion's:
       // viewed and ignored (Sec. 8)
@@ -662,6 +790,8 @@ __device__ inline int insert_rattle(const DevTable& t, Ctx& c) {
         cur = vx.s[0];
         rc = ry;
         moved = true;
+        pend = t.slots + x;
+        pend_v = cur;
       }
     }
     if (!moved && !skip) return ST_CONFLICT;

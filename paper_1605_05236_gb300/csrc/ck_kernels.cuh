@@ -66,6 +66,7 @@ template <int B, int POL, bool GHOST>
 __device__ __forceinline__ int insert_one(const DevTable& t, Ctx& c, uint8_t* region, uint32_t& aborts,
                                           uint64_t* local_e, int local_cap, bool retry_failed = false) {
   c.long_id = -1;
+  c.big_id = -1;
   int st;
   uint32_t fails = 0;
   for (uint32_t attempt = 0;;) {
@@ -82,17 +83,28 @@ __device__ __forceinline__ int insert_one(const DevTable& t, Ctx& c, uint8_t* re
     }
     c.pn = 0;
     st = attempt_insert<B, POL, GHOST>(t, c, region);
+    bool undone = false;
     if (st == ST_OK) {
       if (commit<B>(t, c)) break;
-      st = ST_CONFLICT;  // the terminal free slot was taken: nothing written
+      st = ST_CONFLICT;  // a slot no longer held what the plan expected: its writes were undone
+      undone = true;
     }
-    release_all(t, c);
+    release_all(t, c, undone);
     if (st == ST_LONG) {  // a search path longer than the local plan
       if (c.long_id >= 0 || !grow_plan(t, c)) { st = c.long_id >= 0 ? ST_FAILED : ST_ABORTED; break; }
       continue;
     }
     if (st == ST_FAILED) {
       if (!retry_failed || ++fails > 6) break;
+      // a search out of budget tries again in a larger space (search_space)
+      if (region && c.big_id < 0 && (POL == P_BFS || POL == P_SORTED || POL == P_HYBRID)) {
+        c.big_id = acquire_long(t, c.key ^ 0x5bd1e995u);
+        if (c.big_id >= 0) {
+          uint64_t* vis = reinterpret_cast<uint64_t*>(t.long_scratch + (uint64_t)c.big_id * LONG_REGION + 16 +
+                                                      BIG_GROUPS * sizeof(Group));
+          for (int i = 0; i < BIG_VISITED; i++) vis[i] = 0;  // the region held a plan: no stale tags
+        }
+      }
     } else {
       aborts++;
     }
@@ -102,6 +114,7 @@ __device__ __forceinline__ int insert_one(const DevTable& t, Ctx& c, uint8_t* re
     backoff(st == ST_FAILED ? 6 + 2 * fails : attempt, c.key);
   }
   if (c.long_id >= 0) release_long(t, c.long_id);
+  if (c.big_id >= 0) release_long(t, c.big_id);
   return st;
 }
 
@@ -113,8 +126,25 @@ struct DelPlan {
   uint32_t bin[16];
   uint8_t slot[16];
   uint8_t old_r[16];  // two-choice: duplicate mark; d-ary: rattle counter
+  uint64_t rec;       // the record the copies held when viewed (every copy holds the same)
   int n;
 };
+
+// Replace the record in every claimed copy of p by `to`, each by a 64-bit
+// compare-and-swap from the record seen when the copies were viewed: a
+// claim validates a view through the metadata word only, and that word can
+// come back to an earlier value.  If a copy no longer holds the record, the
+// copies already replaced get it back and the call returns false.
+template <int B>
+__device__ __forceinline__ bool swap_copies(const DevTable& t, const DelPlan& p, uint64_t to) {
+  int done = 0;
+  for (; done < p.n; done++)
+    if (!cas_slot(t.slots + (uint64_t)p.bin[done] * B + p.slot[done], p.rec, to)) break;
+  if (done == p.n) return true;
+  for (int i = 0; i < done; i++) st_slot(t.slots + (uint64_t)p.bin[i] * B + p.slot[i], p.rec);
+  fence_release();
+  return false;
+}
 
 // One delete: find the key in its bins and claim the slots holding it
 // (every copy: a ghost pair has two), clear them, release.  A miss is
@@ -150,8 +180,11 @@ __device__ __forceinline__ int delete_one(const DevTable& t, uint32_t key, DelPl
         }
       }
       if (conflict || !add) continue;
+      uint64_t r0 = slot_of<B>(v, lowest(add));
+      if (any && r0 != p.rec) { conflict = true; break; }  // copies that differ: a writer is active
       if (!cas_acquire(t.meta + b[j], m, m + add)) { conflict = true; break; }
       any = true;
+      p.rec = r0;
       for (int s = 0; s < B; s++) {
         if ((add >> s) & 1u) {
           int i = p.n++;
@@ -166,14 +199,15 @@ __device__ __forceinline__ int delete_one(const DevTable& t, uint32_t key, DelPl
       if (unchanged_since(t.meta, b, seen, nb, CLAIM_BITS)) return 0;
       conflict = true;  // a writer was active in the key's bins: look again
     }
+    bool undone = false;
+    if (!conflict && !swap_copies<B>(t, p, EMPTY)) conflict = undone = true;
     if (conflict) {
-      for (int i = 0; i < p.n; i++) add_relaxed(t.meta + p.bin[i], 0u - (1u << p.slot[i]));
+      for (int i = 0; i < p.n; i++) add_relaxed(t.meta + p.bin[i], (undone ? VER_ONE : 0u) - (1u << p.slot[i]));
       p.n = 0;
       uint32_t w = 128u << (attempt < 13 ? attempt : 13);
       __nanosleep(w + (fmix32(key ^ attempt) & (w - 1)));
       continue;
     }
-    for (int i = 0; i < p.n; i++) st_slot(t.slots + (uint64_t)p.bin[i] * B + p.slot[i], EMPTY);
     for (int i = 0; i < p.n; i++) {
       uint32_t delta = VER_ONE - (1u << p.slot[i]);
       if (B == 1) delta -= (uint32_t)p.old_r[i] << RATTLE_SHIFT;        // the bin forgets r(x)
@@ -215,8 +249,11 @@ __device__ __forceinline__ int update_one(const DevTable& t, uint32_t key, uint6
         }
       }
       if (conflict || !add) continue;
+      uint64_t r0 = slot_of<B>(v, lowest(add));
+      if (any && r0 != p.rec) { conflict = true; break; }  // copies that differ: a writer is active
       if (!cas_acquire(t.meta + b[j], m, m + add)) { conflict = true; break; }
       any = true;
+      p.rec = r0;
       for (int s = 0; s < B; s++) {
         if ((add >> s) & 1u) {
           int i = p.n++;
@@ -229,14 +266,15 @@ __device__ __forceinline__ int update_one(const DevTable& t, uint32_t key, uint6
       if (unchanged_since(t.meta, b, seen, nb, CLAIM_BITS)) return 0;
       conflict = true;
     }
+    bool undone = false;
+    if (!conflict && !swap_copies<B>(t, p, rec)) conflict = undone = true;
     if (conflict) {
-      for (int i = 0; i < p.n; i++) add_relaxed(t.meta + p.bin[i], 0u - (1u << p.slot[i]));
+      for (int i = 0; i < p.n; i++) add_relaxed(t.meta + p.bin[i], (undone ? VER_ONE : 0u) - (1u << p.slot[i]));
       p.n = 0;
       uint32_t w = 128u << (attempt < 13 ? attempt : 13);
       __nanosleep(w + (fmix32(key ^ attempt) & (w - 1)));
       continue;
     }
-    for (int i = 0; i < p.n; i++) st_slot(t.slots + (uint64_t)p.bin[i] * B + p.slot[i], rec);
     fence_release();
     for (int i = 0; i < p.n; i++) red_relaxed(t.meta + p.bin[i], VER_ONE - (1u << p.slot[i]));
     return 1;

@@ -19,11 +19,19 @@
 //
 // The search itself takes no claims.  When it succeeds, every slot of the
 // path is claimed by CAS from the metadata word read when its bin was
-// viewed; a bin that changed since then aborts the attempt.
+// viewed; a bin that changed since then aborts the attempt, and so does a
+// record, read after its claim, that does not belong to the bin the path
+// moves it into (the word came back to its viewed value meanwhile).
 //
 // Per-searcher scratch (global memory, SEARCH_REGION bytes): a 16-byte
 // header holding a generation counter, MAX_GROUPS group records, and an
-// open-addressed visited set tagged with the generation (never cleared).
+// open-addressed visited set tagged with the generation (cleared only when
+// the generation wraps).  In concurrent mode a search that spent its budget
+// without meeting another insertion's claim is retried with four times the
+// budget in a larger space borrowed from the table's scratch plans
+// (search_space): the layout concurrent filling produces differs from the
+// serial one, and a key the serial order places within the budget can need
+// more in it.  The serial replay never retries, so it keeps the budget.
 #pragma once
 #include "ck_insert.cuh"
 
@@ -41,7 +49,49 @@ static_assert(sizeof(Group) == 16, "group record is 16 bytes");
 
 constexpr size_t SEARCH_REGION = 16 + MAX_GROUPS * sizeof(Group) + VISITED_SLOTS * 8;
 
-__device__ __forceinline__ uint32_t vis_hash(uint32_t bin) { return (bin * 0x9E3779B1u) >> (32 - 10); }
+// A larger search space for the retry of a search that ran out of budget in
+// concurrent mode: a scratch plan region (LONG_REGION bytes) holds the
+// header, BIG_GROUPS group records and a visited set of BIG_VISITED slots.
+constexpr int BIG_GROUPS = 2048;
+constexpr int BIG_VISITED = 4096;
+static_assert(16 + BIG_GROUPS * 16 + BIG_VISITED * 8 <= LONG_REGION, "a big search fits a scratch plan region");
+static_assert((1 << 10) == VISITED_SLOTS && (1 << 12) == BIG_VISITED, "visited sets are powers of two");
+
+// Where one search keeps its state, and how much it may use.
+struct SearchSpace {
+  uint32_t* hdr;
+  Group* G;
+  uint64_t* vis;
+  uint32_t max_groups;
+  uint32_t vis_bits;  // the visited set has 2^vis_bits slots
+  uint32_t budget;    // bins viewed
+};
+
+// The ordinary space (the searcher's region, the table's budget), or, when
+// the insertion holds a big region (c.big_id), that region with four times
+// the budget.
+__device__ __forceinline__ SearchSpace search_space(const DevTable& t, const Ctx& c, uint8_t* region) {
+  SearchSpace s;
+  if (c.big_id >= 0) {
+    uint8_t* r = t.long_scratch + (uint64_t)c.big_id * LONG_REGION;
+    s.hdr = reinterpret_cast<uint32_t*>(r);
+    s.G = reinterpret_cast<Group*>(r + 16);
+    s.vis = reinterpret_cast<uint64_t*>(r + 16 + BIG_GROUPS * sizeof(Group));
+    s.max_groups = BIG_GROUPS;
+    s.vis_bits = 12;
+    s.budget = min(4u * t.cap, (uint32_t)BIG_GROUPS - 8u);
+  } else {
+    s.hdr = reinterpret_cast<uint32_t*>(region);
+    s.G = reinterpret_cast<Group*>(region + 16);
+    s.vis = reinterpret_cast<uint64_t*>(region + 16 + MAX_GROUPS * sizeof(Group));
+    s.max_groups = MAX_GROUPS;
+    s.vis_bits = 10;
+    s.budget = t.cap;
+  }
+  return s;
+}
+
+__device__ __forceinline__ uint32_t vis_hash(uint32_t bin, uint32_t bits) { return (bin * 0x9E3779B1u) >> (32 - bits); }
 
 // Bring a bin's slots and metadata word toward L2 ahead of its view.
 template <int B>
@@ -52,19 +102,33 @@ __device__ __forceinline__ void prefetch_bin(const DevTable& t, uint32_t bin) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(t.meta + bin));
 }
 
+// The generation of a new search in a region: one more than the last.  When
+// the 32-bit count wraps, the visited set is cleared (generation 0 marks a
+// free entry and is never used), so a tag left 2^32 searches ago cannot
+// match.
+__device__ __forceinline__ uint32_t next_generation(uint32_t* hdr, uint64_t* vis, uint32_t bits) {
+  uint32_t gen = hdr[0] + 1;
+  if (gen == 0) {
+    for (uint32_t i = 0; i < (1u << bits); i++) vis[i] = 0;
+    gen = 1;
+  }
+  hdr[0] = gen;
+  return gen;
+}
+
 // Insert `bin` into the visited set; returns false if it was already there.
-__device__ __forceinline__ bool vis_insert(uint64_t* vis, uint32_t gen, uint32_t bin) {
+__device__ __forceinline__ bool vis_insert(uint64_t* vis, uint32_t bits, uint32_t gen, uint32_t bin) {
   uint64_t tag = ((uint64_t)gen << 32) | bin;
-  for (uint32_t h = vis_hash(bin);; h = (h + 1) & (VISITED_SLOTS - 1)) {
+  for (uint32_t h = vis_hash(bin, bits);; h = (h + 1) & ((1u << bits) - 1)) {
     uint64_t e = vis[h];
     if (e == tag) return false;
     if ((uint32_t)(e >> 32) != gen) { vis[h] = tag; return true; }
   }
 }
 
-__device__ __forceinline__ bool vis_has(const uint64_t* vis, uint32_t gen, uint32_t bin) {
+__device__ __forceinline__ bool vis_has(const uint64_t* vis, uint32_t bits, uint32_t gen, uint32_t bin) {
   uint64_t tag = ((uint64_t)gen << 32) | bin;
-  for (uint32_t h = vis_hash(bin);; h = (h + 1) & (VISITED_SLOTS - 1)) {
+  for (uint32_t h = vis_hash(bin, bits);; h = (h + 1) & ((1u << bits) - 1)) {
     uint64_t e = vis[h];
     if (e == tag) return true;
     if ((uint32_t)(e >> 32) != gen) return false;
@@ -111,12 +175,11 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
     if (f1) return take_free<B>(t, c, b1, v1, lowest(f1), false);
   }
 
-  uint32_t* hdr = reinterpret_cast<uint32_t*>(region);
-  Group* G = reinterpret_cast<Group*>(region + 16);
-  uint64_t* vis = reinterpret_cast<uint64_t*>(region + 16 + MAX_GROUPS * sizeof(Group));
-  uint32_t gen = hdr[0] + 1;
-  if (gen == 0) gen = 1;
-  hdr[0] = gen;
+  const SearchSpace sp = search_space(t, c, region);
+  Group* G = sp.G;
+  uint64_t* vis = sp.vis;
+  const uint32_t vb = sp.vis_bits;
+  const uint32_t gen = next_generation(sp.hdr, vis, vb);
 
   uint32_t ng = 0, head = 0;
   auto push = [&](uint32_t bin, uint32_t m, uint32_t parent) {
@@ -129,7 +192,7 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
     g.key = (uint16_t)(depth * 16 + spawn_of(m));
     g.stale = 0;
     G[ng++] = g;
-    vis_insert(vis, gen, bin);
+    vis_insert(vis, vb, gen, bin);
   };
   push(b0, v0.m, ~0u);
   push(b1, v1.m, ~0u);
@@ -164,7 +227,7 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
       uint64_t rec = ld_slot(t.slots + (uint64_t)gr.bin * B + s);
       if (rec == EMPTY) continue;
       uint32_t y = other_bin2(t, rec, gr.bin);
-      if (vis_has(vis, gen, y)) continue;
+      if (vis_has(vis, vb, gen, y)) continue;
       if (ORDER != P_BFS && spawn_of(gr.meta) < 15) {
         uint32_t nm = gr.meta + (1u << SPAWN_SHIFT);
         if (cas_acquire(t.meta + gr.bin, gr.meta, nm)) {
@@ -178,8 +241,8 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
           }
         }
       }
-      if (c.viewed - c.viewed0 >= t.cap || ng + nr >= MAX_GROUPS) { out = true; break; }  // budget spent
-      vis_insert(vis, gen, y);
+      if (c.viewed - c.viewed0 >= sp.budget || ng + nr >= sp.max_groups) { out = true; break; }  // budget spent
+      vis_insert(vis, vb, gen, y);
       c.viewed++;
       prefetch_bin<B>(t, y);
       rg[nr] = g;
@@ -227,7 +290,12 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
         if (gq.stale) return ST_CONFLICT;
         if (!cas_acquire(t.meta + gq.bin, gq.meta, gq.meta + (1u << sl))) return ST_CONFLICT;
         c.pn = (int)e + 1;
-        set_content(c, (int)e, ld_slot(t.slots + (uint64_t)gq.bin * B + sl));
+        // the record must move into the next bin of the path: it is the one
+        // the search saw unless the bin's word came back to its viewed value
+        const uint64_t r = reread<B>(t, gq.bin, sl);
+        const uint32_t to = e + 1 < depth ? G[(uint32_t)content_at(c, (int)e + 1)].bin : y;
+        set_content(c, (int)e, r);
+        if (!belongs<B>(t, r, to)) return ST_CONFLICT;
       }
       c.kicks = depth;
       if (isdup) return take_dup<B>(t, c, y, vy, term, false);
@@ -262,12 +330,11 @@ __device__ int insert_search_dary(const DevTable& t, Ctx& c, uint8_t* region) {
     if (free_mask<1>(v[i])) return take_free<1>(t, c, b[i], v[i], 0, false);
   }
 
-  uint32_t* hdr = reinterpret_cast<uint32_t*>(region);
-  Group* G = reinterpret_cast<Group*>(region + 16);
-  uint64_t* vis = reinterpret_cast<uint64_t*>(region + 16 + MAX_GROUPS * sizeof(Group));
-  uint32_t gen = hdr[0] + 1;
-  if (gen == 0) gen = 1;
-  hdr[0] = gen;
+  const SearchSpace sp = search_space(t, c, region);
+  Group* G = sp.G;
+  uint64_t* vis = sp.vis;
+  const uint32_t vb = sp.vis_bits;
+  const uint32_t gen = next_generation(sp.hdr, vis, vb);
 
   uint32_t ng = 0, head = 0;
   auto push = [&](uint32_t bin, uint32_t m, uint32_t parent) {
@@ -280,7 +347,7 @@ __device__ int insert_search_dary(const DevTable& t, Ctx& c, uint8_t* region) {
     g.key = (uint16_t)(depth * 16 + spawn_of(m));
     g.stale = 0;
     G[ng++] = g;
-    vis_insert(vis, gen, bin);
+    vis_insert(vis, vb, gen, bin);
   };
   for (uint32_t i = 0; i < d; i++) push(b[i], v[i].m, ~0u);
 
@@ -312,7 +379,7 @@ __device__ int insert_search_dary(const DevTable& t, Ctx& c, uint8_t* region) {
       uint32_t rb[4];
       bins_of(t, key_of(rec), rb);
       uint32_t y = rb[j];
-      if (y == gr.bin || vis_has(vis, gen, y)) continue;
+      if (y == gr.bin || vis_has(vis, vb, gen, y)) continue;
       if (ORDER != P_BFS && spawn_of(gr.meta) < 15) {
         uint32_t nm = gr.meta + (1u << SPAWN_SHIFT);
         if (cas_acquire(t.meta + gr.bin, gr.meta, nm)) {
@@ -326,8 +393,8 @@ __device__ int insert_search_dary(const DevTable& t, Ctx& c, uint8_t* region) {
           }
         }
       }
-      if (c.viewed - c.viewed0 >= t.cap || ng + nr >= MAX_GROUPS) { out = true; break; }  // budget spent
-      vis_insert(vis, gen, y);
+      if (c.viewed - c.viewed0 >= sp.budget || ng + nr >= sp.max_groups) { out = true; break; }  // budget spent
+      vis_insert(vis, vb, gen, y);
       c.viewed++;
       prefetch_bin<1>(t, y);
       rg[nr] = g;
@@ -363,7 +430,10 @@ __device__ int insert_search_dary(const DevTable& t, Ctx& c, uint8_t* region) {
         if (gq.stale) return ST_CONFLICT;
         if (!cas_acquire(t.meta + gq.bin, gq.meta, gq.meta + 1u)) return ST_CONFLICT;
         c.pn = (int)e + 1;
-        set_content(c, (int)e, ld_slot(t.slots + gq.bin));
+        const uint64_t r = reread<1>(t, gq.bin, 0);
+        const uint32_t to = e + 1 < depth ? G[(uint32_t)content_at(c, (int)e + 1)].bin : y;
+        set_content(c, (int)e, r);
+        if (!belongs<1>(t, r, to)) return ST_CONFLICT;
       }
       c.kicks = depth;
       return take_free<1>(t, c, y, vy, 0, false);
