@@ -186,6 +186,16 @@ unsigned grid_for(uint64_t n, uint32_t block) {
 // Device view of a handle, for the other translation units of the library.
 const ck::DevTable* ck_internal_devtable(const ck_table* t) { return &t->dt; }
 
+// Keys submitted for insertion so far (the bins-viewed histogram's load).
+uint64_t ck_internal_load_base(const ck_table* t) { return t->load_base; }
+
+// Bookkeeping of an insert launch made by another translation unit: the
+// handle's readers wait for its stream, and the load base moves on.
+void ck_internal_note_insert(ck_table* t, void* stream, uint64_t n) {
+  t->last = S(stream);
+  t->load_base += n;
+}
+
 // The stream that host-side reads of the table (stats, export) wait for;
 // the serving loop hands it back when it lets go of the table.
 void* ck_internal_swap_last(ck_table* t, void* s) {

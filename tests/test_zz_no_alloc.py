@@ -34,18 +34,38 @@ def ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-@pytest.mark.parametrize("policy", [ck.SORTED | ck.GHOST, ck.BFS, ck.QUEUE])
-def test_noalloc_matches_insert_batch(policy):
+# (policy, bins, slots per bin, choices, load before the two calls, chain cap):
+# every kind of insertion the entry point runs -- walks (which retry a
+# failed attempt, as ck_insert_batch's concurrent mode does), searches, 4-
+# and 8-slot bins, single-slot d-ary bins -- ending at loads where walks
+# fail and are retried
+CASES = [
+    (ck.SORTED | ck.GHOST, 1 << 11, 4, 2, 0.80, 500),
+    (ck.BFS, 1 << 13, 4, 2, 0.93, 500),
+    (ck.QUEUE, 1 << 13, 4, 2, 0.93, 500),
+    (ck.RANDOM, 1 << 13, 4, 2, 0.93, 500),
+    (ck.RANDOM, 1 << 12, 8, 2, 0.95, 500),
+    (ck.SORTED, 1 << 12, 8, 2, 0.95, 500),
+    (ck.RANDOM, 1 << 15, 1, 3, 0.86, 4096),
+    (ck.RATTLE, 1 << 15, 1, 4, 0.93, 500),
+    (ck.BFS, 1 << 15, 1, 4, 0.88, 500),
+]
+
+
+@pytest.mark.parametrize("policy,bins,B,d,load,cap", CASES,
+                         ids=["%x-%d-B%d-d%d-%.2f" % (c[0], c[1], c[2], c[3], c[4]) for c in CASES])
+def test_noalloc_matches_insert_batch(policy, bins, B, d, load, cap):
     f = noalloc_fn()
     stream = torch.cuda.current_stream()
-    bins, B = 1 << 11, 4
-    keys, _ = inputs.distinct_keys(inputs.load_target(bins * B, 0.80) + 2 * MAX_KEYS, 91)
+    keys, _ = inputs.distinct_keys(inputs.load_target(bins * B, load) + 2 * MAX_KEYS, 91)
     vals = inputs.values_for(keys)
     pre = len(keys) - 2 * MAX_KEYS
     kt, vt = ck.as_u32_tensor(keys), ck.as_u32_tensor(vals)
-    a = ck.CuckooTable(bins, B, 2, policy, seed=3)  # filled through the new entry point
-    b = ck.CuckooTable(bins, B, 2, policy, seed=3)  # filled through ck_insert_batch
-    # identical starting tables at load 0.80 (serial replay gives one layout)
+    a = ck.CuckooTable(bins, B, d, policy, seed=3)  # filled through the new entry point
+    b = ck.CuckooTable(bins, B, d, policy, seed=3)  # filled through ck_insert_batch
+    for t in (a, b):
+        t.set_param(ck.PARAM_CHAIN_CAP, cap)
+    # identical starting tables (serial replay gives one layout)
     a.insert(kt[:pre], vt[:pre], serial=True)
     b.insert(kt[:pre], vt[:pre], serial=True)
     torch.cuda.synchronize()
@@ -62,6 +82,13 @@ def test_noalloc_matches_insert_batch(policy):
         assert a.contents() == b.contents()
     sa, sb = a.stats(), b.stats()
     assert sa["size"] == sb["size"] == len(keys)
+    assert sa["inserts_ok"] == sb["inserts_ok"] == len(keys)
+    # both calls' insertions are in the histograms, at the loads they ran at
+    va, ca = a.load_histogram()
+    vb, cb = b.load_histogram()
+    assert int(ca.sum()) == int(cb.sum()) == len(keys)
+    assert np.array_equal(ca, cb)
+    assert int(a.chain_histogram().sum()) == int(b.chain_histogram().sum()) == len(keys)
     # lookups read both tables alike
     va, fa = a.lookup(kt)
     vb, fb = b.lookup(kt)
