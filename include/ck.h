@@ -231,8 +231,10 @@ const char *ck_strerror(int code);
  * For callers that must not allocate device memory on their insertion path:
  * services whose device memory budget is fixed up front, real-time sections
  * where an allocation's latency is not acceptable, libraries embedding this
- * one that own no device allocator.  Same operation and per-key status as ck_insert_batch, but the
- * per-search scratch of breadth-first and sorted search comes from a fixed
+ * one that own no device allocator.  Same operation and per-key status as
+ * ck_insert_batch (the key -> value map it leaves is the one ck_insert_batch
+ * leaves for the same keys; the slot layout may differ, as between any two
+ * concurrent runs), but the per-search scratch of breadth-first and sorted search comes from a fixed
  * array compiled into libck.so (CK_NOALLOC_MAX_KEYS regions of 16,400 bytes,
  * 8.0 MiB, in the memory of every GPU that loads the library, kept until the
  * process exits), one region per key, and the call allocates nothing.
@@ -244,9 +246,13 @@ const char *ck_strerror(int code);
  *     (other streams, other tables) race on it and must be ordered by the
  *     caller.  The array keeps the last call's contents; nothing in it has
  *     to start at zero.
- *   - The table's counters are updated; the load histogram is not.
- *   - Insertions are concurrent (one thread per key) as in ck_insert_batch;
- *     the launch does not overlap the previous insert launch. */
+ *   - The table's counters, bins-viewed-by-load histogram and chain-length
+ *     histogram are updated as ck_insert_batch updates them, and the
+ *     handle's readers (ck_stats, the histograms, ck_export) wait for this
+ *     call's stream.
+ *   - Insertions are concurrent (one thread per key) as in ck_insert_batch's
+ *     concurrent mode, failed walks retried the same way; the launch does
+ *     not overlap the previous insert launch. */
 #define CK_NOALLOC_MAX_KEYS 512
 int ck_insert_batch_noalloc(ck_table *t, const uint32_t *d_keys, const uint32_t *d_vals, uint64_t n,
                             uint8_t *d_status, void *stream);
@@ -312,6 +318,31 @@ int ck_multi_export(ck_multi *m, uint32_t table, uint64_t *h_slots, uint32_t *h_
 /* Empty every table (asynchronous) / free the handle (not the buffer). */
 int ck_multi_clear(ck_multi *m, void *stream);
 void ck_multi_destroy(ck_multi *m);
+
+/* A batched fill captured once and replayed as a CUDA graph: launching the
+ * thousands of operations of a fill (a clear is three copies per table;
+ * the per-table path launches one kernel per table) costs the host more
+ * than the GPU spends on them, and a graph replays them with one call.
+ * ck_multi_capture records, on `stream` (NULL: a stream of the library's
+ * own), an optional clear of every table (CK_MULTI_CAPTURE_CLEAR) followed
+ * by ck_multi_insert -- or ck_multi_insert_per_table with
+ * CK_MULTI_CAPTURE_PER_TABLE -- of the given device arrays, and
+ * instantiates it; nothing runs until ck_graph_launch.  The graph keeps the
+ * pointers and launch shape of the capture: replaying it fills the same
+ * arrays into the same tables (capture again after ck_multi_set_param or
+ * for other arrays).  Capture mode is thread-local, so other host threads
+ * may use CUDA meanwhile; `stream` must not be capturing already.
+ * Returns CK_EINVAL for bad arguments or flags, CK_ECUDA if the capture or
+ * instantiation fails (no handle is returned then).  ck_graph_launch is
+ * asynchronous on `stream`; the batched handle's readers then wait for that
+ * stream.  ck_graph_destroy frees the graph (not the tables). */
+typedef struct ck_graph ck_graph;
+#define CK_MULTI_CAPTURE_CLEAR 1u
+#define CK_MULTI_CAPTURE_PER_TABLE 2u
+int ck_multi_capture(ck_multi *m, const uint32_t *d_keys, const uint32_t *d_vals, uint8_t *d_status,
+                     uint32_t flags, void *stream, ck_graph **out);
+int ck_graph_launch(ck_graph *g, void *stream);
+void ck_graph_destroy(ck_graph *g);
 
 /* ---- serving form: a continuous-batching request loop ----
  *
@@ -497,6 +528,16 @@ int ck_debug_claims(ck_table *t, uint64_t bin, uint32_t set_mask, uint32_t clear
  * 8 KB of device memory the kernel may write.  Asynchronous. */
 int ck_gather_probe(const void *d_buf, size_t bytes, uint32_t width, uint64_t n_reads,
                     uint64_t seed, void *d_sink, void *stream);
+
+/* The same reads with the launch shape given, for finding the fastest one
+ * (the roofline is the best the memory system gives this pattern):
+ * per_thread independent reads in flight per thread (1, 2, 4 or 8), `block`
+ * threads per block (a multiple of 32, at most 1024), at most `max_blocks`
+ * blocks striding over the reads (0: as many blocks as it takes for one
+ * pass).  ck_gather_probe is per_thread 8, block 256, max_blocks 152 * 64.
+ * CK_EINVAL for any other value; asynchronous. */
+int ck_gather_probe_ex(const void *d_buf, size_t bytes, uint32_t width, uint64_t n_reads, uint64_t seed,
+                       uint32_t per_thread, uint32_t block, uint32_t max_blocks, void *d_sink, void *stream);
 
 /* Measurement helper (not an operation of the paper): n_ops independent
  * random atomics over a device buffer of `bytes` bytes (64-byte aligned),

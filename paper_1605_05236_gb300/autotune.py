@@ -27,16 +27,18 @@ def _fill_ms(mt, kt, vt, st, stream, reps=1):
     return best
 
 
-def tune(mt, kt, vt, st, stream=None, blocks=(128, 256), per_sm=(0, 4), tiles=(1024, 4096, 16384)):
-    """Try every (block, blocks_per_sm, tile) combination once; leave the
-    best one set on `mt` and return (best, [(config, ms), ...])."""
+def tune(mt, kt, vt, st, stream=None, blocks=(128, 256), per_sm=(0, 4), tiles=(1024, 4096, 16384), reps=3):
+    """Time every (block, blocks_per_sm, tile) combination, each the best of
+    `reps` fills (the first fill of a shape also warms it); leave the
+    fastest set on `mt` and return (best, [(config, ms), ...])."""
     stream = stream or torch.cuda.current_stream()
     results = []
     for b, p, t in itertools.product(blocks, per_sm, tiles):
         mt.set_param(M.MULTI_BLOCK, b)
         mt.set_param(M.MULTI_BLOCKS_PER_SM, p)
         mt.set_param(M.MULTI_TILE, t)
-        results.append(({"block": b, "blocks_per_sm": p, "tile": t}, _fill_ms(mt, kt, vt, st, stream)))
+        _fill_ms(mt, kt, vt, st, stream)  # warm-up
+        results.append(({"block": b, "blocks_per_sm": p, "tile": t}, _fill_ms(mt, kt, vt, st, stream, reps)))
     best = min(results, key=lambda r: r[1])[0]
     mt.set_param(M.MULTI_BLOCK, best["block"])
     mt.set_param(M.MULTI_BLOCKS_PER_SM, best["blocks_per_sm"])

@@ -86,6 +86,7 @@ def load(build_if_missing: bool = True):
     L.ck_shape.argtypes = [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u32), ctypes.POINTER(_u32),
                            ctypes.POINTER(_u32)]
     L.ck_gather_probe.argtypes = [_vp, ctypes.c_size_t, _u32, _u64, _u64, _vp, _vp]
+    L.ck_gather_probe_ex.argtypes = [_vp, ctypes.c_size_t, _u32, _u64, _u64, _u32, _u32, _u32, _vp, _vp]
     L.ck_atomic_probe.argtypes = [_vp, ctypes.c_size_t, _u32, _u64, _u64, _vp, _vp]
     L.ck_import.argtypes = [_vp, _vp, _vp]
     L.ck_debug_claims.argtypes = [_vp, _u64, _u32, _u32]
@@ -286,6 +287,14 @@ def gather_probe(buf: torch.Tensor, width: int, n_reads: int, seed: int, sink: t
     rc = load().ck_gather_probe(_ptr(buf), buf.numel() * buf.element_size(), width, n_reads, seed,
                                 _ptr(sink), _stream(stream))
     _check(rc, "ck_gather_probe")
+
+
+def gather_probe_ex(buf: torch.Tensor, width: int, n_reads: int, seed: int, per_thread: int, block: int,
+                    max_blocks: int, sink: torch.Tensor, stream=None):
+    """Random reads with a given launch shape (see ck_gather_probe_ex)."""
+    rc = load().ck_gather_probe_ex(_ptr(buf), buf.numel() * buf.element_size(), width, n_reads, seed, per_thread,
+                                   block, max_blocks, _ptr(sink), _stream(stream))
+    _check(rc, "ck_gather_probe_ex")
 
 
 def atomic_probe(buf: torch.Tensor, kind: int, n_ops: int, seed: int, sink: torch.Tensor, stream=None):

@@ -561,6 +561,76 @@ int ck_multi_clear(ck_multi* m, void* stream) {
   return clear_tables(m, reinterpret_cast<cudaStream_t>(stream));
 }
 
+}  // extern "C"
+
+// A captured fill of a batched form: the graph and its executable.
+struct ck_graph {
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  ck_multi* m;
+};
+
+extern "C" {
+
+int ck_multi_capture(ck_multi* m, const uint32_t* d_keys, const uint32_t* d_vals, uint8_t* d_status,
+                     uint32_t flags, void* stream, ck_graph** out) {
+  if (!out) return CK_EINVAL;
+  *out = nullptr;
+  if (!m || !d_keys || !d_vals) return CK_EINVAL;
+  if (flags & ~(uint32_t)(CK_MULTI_CAPTURE_CLEAR | CK_MULTI_CAPTURE_PER_TABLE)) return CK_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  bool own = false;
+  if (!s) {  // the legacy default stream cannot be captured: use a stream of our own
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return CK_ECUDA;
+    own = true;
+  }
+  const cudaStream_t last = m->last;
+  int rc = CK_OK;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = CK_ECUDA;
+  if (rc == CK_OK) {
+    if (flags & CK_MULTI_CAPTURE_CLEAR) rc = clear_tables(m, s);
+    if (rc == CK_OK)
+      rc = (flags & CK_MULTI_CAPTURE_PER_TABLE) ? ck_multi_insert_per_table(m, d_keys, d_vals, d_status, s)
+                                                : ck_multi_insert(m, d_keys, d_vals, d_status, s);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);  // always ends the capture, even after an error
+    if (rc == CK_OK && (e != cudaSuccess || !g)) rc = CK_ECUDA;
+    ck_graph* h = nullptr;
+    if (rc == CK_OK) {
+      h = new (std::nothrow) ck_graph();
+      if (!h) rc = CK_ENOMEM;
+    }
+    if (rc == CK_OK && cudaGraphInstantiate(&h->exec, g, 0) != cudaSuccess) rc = CK_ECUDA;
+    if (rc == CK_OK) {
+      h->graph = g;
+      h->m = m;
+      *out = h;
+    } else {
+      if (g) cudaGraphDestroy(g);
+      delete h;
+      cudaGetLastError();
+    }
+  }
+  m->last = last;  // nothing ran yet: the handle's readers keep waiting where they did
+  if (own) cudaStreamDestroy(s);
+  return rc;
+}
+
+int ck_graph_launch(ck_graph* g, void* stream) {
+  if (!g) return CK_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaGraphLaunch(g->exec, s) != cudaSuccess) return CK_ECUDA;
+  g->m->last = s;
+  return CK_OK;
+}
+
+void ck_graph_destroy(ck_graph* g) {
+  if (!g) return;
+  cudaGraphExecDestroy(g->exec);
+  cudaGraphDestroy(g->graph);
+  delete g;
+}
+
 void ck_multi_destroy(ck_multi* m) {
   if (!m) return;
   if (m->last) cudaStreamSynchronize(m->last);

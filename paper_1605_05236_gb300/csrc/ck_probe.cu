@@ -20,11 +20,12 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-template <int W>  // bytes per record: 8, 32 or 64
-__global__ void __launch_bounds__(256) k_gather(const uint64_t* __restrict__ buf, uint64_t n_records,
-                                                uint64_t mask, uint64_t n_reads, uint64_t seed,
-                                                uint64_t* __restrict__ sink) {
-  constexpr int U = 8;  // independent reads in flight per thread
+// U independent random reads in flight per thread, each of one W-byte
+// record (8, 32 or 64 bytes).  A grid of gridDim.x blocks strides over the
+// reads; a grid that covers every read once makes each thread do one pass.
+template <int W, int U>
+__global__ void k_gather(const uint64_t* __restrict__ buf, uint64_t n_records, uint64_t mask, uint64_t n_reads,
+                         uint64_t seed, uint64_t* __restrict__ sink) {
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   uint64_t acc = 0;
@@ -56,6 +57,18 @@ __global__ void __launch_bounds__(256) k_gather(const uint64_t* __restrict__ buf
       for (int q = 0; q < W / 8; q++) acc ^= v[u][q];
   }
   if (acc == 0x0123456789ABCDEFull) sink[tid & 1023] = acc;  // keeps the loads live
+}
+
+template <int W>
+cudaError_t launch_gather(uint32_t per_thread, unsigned grid, unsigned block, cudaStream_t s, const uint64_t* b,
+                          uint64_t n_records, uint64_t mask, uint64_t n_reads, uint64_t seed, uint64_t* k) {
+  switch (per_thread) {
+    case 1: k_gather<W, 1><<<grid, block, 0, s>>>(b, n_records, mask, n_reads, seed, k); break;
+    case 2: k_gather<W, 2><<<grid, block, 0, s>>>(b, n_records, mask, n_reads, seed, k); break;
+    case 4: k_gather<W, 4><<<grid, block, 0, s>>>(b, n_records, mask, n_reads, seed, k); break;
+    default: k_gather<W, 8><<<grid, block, 0, s>>>(b, n_records, mask, n_reads, seed, k); break;
+  }
+  return cudaGetLastError();
 }
 
 // KIND 0: red.add.u32 (no result), 1: atom.add.u32 (result used),
@@ -112,21 +125,32 @@ extern "C" int ck_atomic_probe(void* d_buf, size_t bytes, uint32_t kind, uint64_
   return cudaGetLastError() == cudaSuccess ? CK_OK : CK_ECUDA;
 }
 
-extern "C" int ck_gather_probe(const void* d_buf, size_t bytes, uint32_t width, uint64_t n_reads,
-                               uint64_t seed, void* d_sink, void* stream) {
+extern "C" int ck_gather_probe_ex(const void* d_buf, size_t bytes, uint32_t width, uint64_t n_reads, uint64_t seed,
+                                  uint32_t per_thread, uint32_t block, uint32_t max_blocks, void* d_sink,
+                                  void* stream) {
   if (!d_buf || !d_sink || (width != 8 && width != 32 && width != 64)) return CK_EINVAL;
+  if (per_thread != 1 && per_thread != 2 && per_thread != 4 && per_thread != 8) return CK_EINVAL;
+  if (block < 32 || block > 1024 || (block % 32) != 0) return CK_EINVAL;
   if ((reinterpret_cast<uintptr_t>(d_buf) % 64) != 0 || bytes < 64) return CK_EINVAL;
   uint64_t n_records = bytes / width;
   uint64_t mask = (n_records & (n_records - 1)) == 0 ? n_records - 1 : 0;
-  uint64_t threads = (n_reads + 7) / 8;
-  uint64_t grid = (threads + 255) / 256;
-  if (grid > 152ull * 64) grid = 152ull * 64;  // grid-stride beyond a few waves
+  uint64_t threads = (n_reads + per_thread - 1) / per_thread;
+  uint64_t grid = (threads + block - 1) / block;
+  if (max_blocks && grid > max_blocks) grid = max_blocks;  // grid-stride beyond max_blocks
+  if (grid > 0x7FFFFFFFull) grid = 0x7FFFFFFFull;
   if (grid == 0) grid = 1;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const uint64_t* b = static_cast<const uint64_t*>(d_buf);
   uint64_t* k = static_cast<uint64_t*>(d_sink);
-  if (width == 8) k_gather<8><<<(unsigned)grid, 256, 0, s>>>(b, n_records, mask, n_reads, seed, k);
-  else if (width == 32) k_gather<32><<<(unsigned)grid, 256, 0, s>>>(b, n_records, mask, n_reads, seed, k);
-  else k_gather<64><<<(unsigned)grid, 256, 0, s>>>(b, n_records, mask, n_reads, seed, k);
-  return cudaGetLastError() == cudaSuccess ? CK_OK : CK_ECUDA;
+  cudaError_t e;
+  if (width == 8) e = launch_gather<8>(per_thread, (unsigned)grid, block, s, b, n_records, mask, n_reads, seed, k);
+  else if (width == 32) e = launch_gather<32>(per_thread, (unsigned)grid, block, s, b, n_records, mask, n_reads, seed, k);
+  else e = launch_gather<64>(per_thread, (unsigned)grid, block, s, b, n_records, mask, n_reads, seed, k);
+  return e == cudaSuccess ? CK_OK : CK_ECUDA;
+}
+
+extern "C" int ck_gather_probe(const void* d_buf, size_t bytes, uint32_t width, uint64_t n_reads,
+                               uint64_t seed, void* d_sink, void* stream) {
+  // 8 reads in flight per thread, 256-thread blocks, at most 64 blocks per SM of 152
+  return ck_gather_probe_ex(d_buf, bytes, width, n_reads, seed, 8, 256, 152u * 64u, d_sink, stream);
 }

@@ -10,6 +10,7 @@ import torch
 from . import ck
 
 MULTI_TILE, MULTI_BLOCK, MULTI_BLOCKS_PER_SM, MULTI_CHAIN_CAP = 1, 2, 3, 4
+CAPTURE_CLEAR, CAPTURE_PER_TABLE = 1, 2
 
 
 class MultiDesc(ctypes.Structure):
@@ -38,6 +39,10 @@ def _lib():
         L.ck_multi_clear.argtypes = [vp, vp]
         L.ck_multi_destroy.argtypes = [vp]
         L.ck_multi_destroy.restype = None
+        L.ck_multi_capture.argtypes = [vp, vp, vp, vp, u32, vp, ctypes.POINTER(vp)]
+        L.ck_graph_launch.argtypes = [vp, vp]
+        L.ck_graph_destroy.argtypes = [vp]
+        L.ck_graph_destroy.restype = None
         _bound = True
     return L
 
@@ -53,6 +58,28 @@ def _descs(bins, slots, n_keys):
         arr[i].n_keys = int(n_keys[i])
         off += int(n_keys[i])
     return arr
+
+
+class Graph:
+    """A captured batched fill (ck_multi_capture): launch() replays it."""
+
+    def __init__(self, handle, table):
+        self._h = handle
+        self._table = table  # keeps the tables (and their buffer) alive
+
+    def launch(self, stream=None):
+        ck._check(_lib().ck_graph_launch(self._h, ck._stream(stream)), "ck_graph_launch")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().ck_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class MultiTable:
@@ -97,6 +124,15 @@ class MultiTable:
         f = _lib().ck_multi_insert_per_table if per_table else _lib().ck_multi_insert
         ck._check(f(self._h, ck._ptr(keys), ck._ptr(vals), ck._ptr(status), ck._stream(stream)), "ck_multi_insert")
         return status
+
+    def capture(self, keys, vals, status=None, per_table=False, clear=True, stream=None) -> "Graph":
+        """Capture a fill (optionally after clearing every table) as a CUDA
+        graph; Graph.launch() runs it.  The arrays must outlive the graph."""
+        flags = (CAPTURE_CLEAR if clear else 0) | (CAPTURE_PER_TABLE if per_table else 0)
+        h = ctypes.c_void_p()
+        ck._check(_lib().ck_multi_capture(self._h, ck._ptr(keys), ck._ptr(vals), ck._ptr(status), flags,
+                                          ck._stream(stream), ctypes.byref(h)), "ck_multi_capture")
+        return Graph(h, self)
 
     def lookup(self, tab, keys, vals=None, found=None, stream=None):
         n = keys.numel()

@@ -65,7 +65,7 @@ def test_gpu_arm_bench_line_is_compact_and_last():
                             "all_cores": {"cores": 16, "m_lookups_per_s": 200.0, "m_deletes_per_s": 150.0},
                             "host": {"nproc": 16, "machine": "aarch64", "cpu": "c" * 80}},
            "sections": {"policies": big, "transactional": big},
-           "section_summary": {"policies": {"queue_vs_random_bins_viewed": [2.28, 3.9], "failed_total": 0,
+           "section_summary": {"policies": {"queue_vs_random_viewed_at_0.95": [7.5, 18.4], "failed_total": 0,
                                             "contents_exact": True},
                                "batched_form": {"speedup_vs_per_table": 1.77, "m_inserts_per_s": 900.0,
                                                 "all_inserted": True},

@@ -69,3 +69,26 @@ def test_full_size_fill_lookups_deletes_match_the_oracle():
     _, f2 = t.lookup(ck.as_u32_tensor(dk))
     assert not f2.cpu().numpy().any()
     assert t.stats()["size"] == n - len(dk)
+
+
+def test_l2_resident_small_table_matches_the_oracle():
+    """The small-table workload at its full size and launch configuration:
+    2^14 bins x 4 slots (512 KiB of slots, L2-resident), 62,259 keys of seed
+    1 inserted by one call with random kicking, chain cap 500, then 65,536
+    lookups (half present, half absent, shuffled).  The concurrent GPU fill
+    holds exactly the serial oracle's key -> value set and answers every
+    lookup as the oracle does."""
+    keys, vals, lk, expect = bench.small_table_workload()
+    t = ck.CuckooTable(bench.SMALL_BINS, bench.B, 2, ck.RANDOM, seed=1)
+    t.set_param(ck.PARAM_CHAIN_CAP, 500)
+    st = t.insert(ck.as_u32_tensor(keys), ck.as_u32_tensor(vals)).cpu().numpy()
+    ref = oracle.OracleTable(bench.SMALL_BINS, bench.B, 2, oracle.RANDOM, rng_seed=1, cap=500)
+    ost = ref.insert(keys, vals)
+    assert (ost == 0).all() and (st == 0).all(), np.bincount(st)
+    assert t.contents() == ref.contents()
+    slots, meta = t.export()
+    assert check_table(slots, meta, bench.SMALL_BINS, bench.B, 2)["size"] == len(keys)
+    v, f = t.lookup(ck.as_u32_tensor(lk))
+    ov, of = ref.lookup(lk)
+    assert np.array_equal(f.cpu().numpy(), of) and np.array_equal(of, expect)
+    assert np.array_equal(ck.u32_numpy(v), ov)

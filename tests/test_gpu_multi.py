@@ -73,3 +73,35 @@ def test_batched_invariants_and_clear():
         meta = np.zeros(int(bins[i]), dtype=np.uint32)
         M._lib().ck_multi_export(m._h, i, None, meta.ctypes.data_as(ctypes.c_void_p))
         check_table(slots_i, meta, int(bins[i]), int(slots[i]), 2)
+
+
+@pytest.mark.parametrize("per_table", [False, True])
+def test_captured_fill_replays_exactly(per_table):
+    """ck_multi_capture: a clear + fill captured once as a CUDA graph and
+    launched three times leaves every table holding exactly its keys (the
+    serial oracle's map for the first tables), and the counters of the last
+    replay."""
+    bins, slots, keys, vals, n_keys = small_workload(32, seed=13)
+    kt, vt = ck.as_u32_tensor(keys), ck.as_u32_tensor(vals)
+    st = torch.full((len(keys),), 255, dtype=torch.uint8, device="cuda")
+    m = M.MultiTable(bins, slots, n_keys, ck.QUEUE, seed=3)
+    g = m.capture(kt, vt, st, per_table=per_table, clear=True)
+    torch.cuda.synchronize()
+    assert bool((st == 255).all()), "capture ran work"
+    side = torch.cuda.Stream()
+    for _ in range(3):
+        g.launch(side)
+    side.synchronize()
+    assert bool((st == 0).all())
+    assert m.stats()["size"] == len(keys)  # cleared before each fill: counts of one fill
+    off = 0
+    for i in range(len(bins)):
+        n = int(n_keys[i])
+        want = {int(k): int(v) for k, v in zip(keys[off:off + n], vals[off:off + n])}
+        assert m.contents(i) == want, i
+        if i < 4:
+            ref = oracle.OracleTable(int(bins[i]), int(slots[i]), 2, ck.QUEUE, rng_seed=3 + i)
+            assert (ref.insert(keys[off:off + n], vals[off:off + n]) == 0).all()
+            assert ref.contents() == want
+        off += n
+    g.close()
