@@ -294,10 +294,6 @@ __device__ __forceinline__ void load_view(const DevTable& t, uint32_t bin, View<
   }
 }
 
-// Views of a key's two bins with one wait: both metadata words (relaxed),
-// one acquire fence, then both bins' slots, so each view's slots are read
-// after its metadata word (what load_view's acquire gives) at the cost of
-// two round trips instead of three.
 template <int B>
 __device__ __forceinline__ void load_slots(const DevTable& t, uint32_t bin, View<B>& v) {
   const uint64_t* p = t.slots + (uint64_t)bin * B;
@@ -309,21 +305,24 @@ __device__ __forceinline__ void load_slots(const DevTable& t, uint32_t bin, View
   }
 }
 
-// A view without ordering between the metadata word and the slots, for a
-// placement into a free slot (validated by the slot's own compare-and-swap).
-// Before a claim is taken on it, the slots are read again after an acquire
-// fence (reread_slots), which restores load_view's order.
+// A view without ordering between the metadata word and the slots, in one
+// round trip.  Insertions plan on such views: a free slot they take is
+// written by a compare-and-swap from empty, and every record they move is
+// read again after its claim (reread) -- so a view whose slots are older or
+// newer than its word costs a retry, never a wrong move.  Deletes, which
+// prove misses from their views, use load_view.
 template <int B>
 __device__ __forceinline__ void load_view_fast(const DevTable& t, uint32_t bin, View<B>& v) {
   v.m = ld_relaxed(t.meta + bin);
   load_slots<B>(t, bin, v);
 }
 
+// Views of a key's two bins in one round trip (unordered, as load_view_fast).
 template <int B>
-__device__ __forceinline__ void load_view2(const DevTable& t, uint32_t b0, uint32_t b1, View<B>& v0, View<B>& v1) {
+__device__ __forceinline__ void load_view2_fast(const DevTable& t, uint32_t b0, uint32_t b1, View<B>& v0,
+                                                View<B>& v1) {
   v0.m = ld_relaxed(t.meta + b0);
   v1.m = ld_relaxed(t.meta + b1);
-  fence_acquire();
   load_slots<B>(t, b0, v0);
   load_slots<B>(t, b1, v1);
 }

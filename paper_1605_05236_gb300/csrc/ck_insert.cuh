@@ -222,16 +222,18 @@ __device__ __forceinline__ bool claim_again(const DevTable& t, Ctx& c, uint32_t 
 }
 
 // A new key straight into free slot s of `bin` (tables without ghosts):
-// one 64-bit compare-and-swap of the slot from empty to the record, then a
-// relaxed add that advances the bin's version (and, for queue-kicking, its
-// hit counter).  No claim is taken: the key moves nothing, and a chain that
-// had claimed this slot as its terminal finds it taken when it commits and
-// starts again.  With one insertion in flight the slot and the metadata
-// word end exactly as a claim and its release would leave them.
+// one 64-bit compare-and-swap of the slot from empty to the record, and for
+// queue-kicking a relaxed add that advances the bin's hit counter (Sec. 6:
+// every placement into a bin counts).  No claim is taken and the version
+// does not move: the key moves nothing, so no reader that proves a miss and
+// no planner's claim depends on it (a chain that had claimed this slot as
+// its terminal finds it taken when its compare-and-swap commits, and starts
+// again).  With one insertion in flight the slot and the policy's metadata
+// end exactly as a claim and its release would leave them.
 template <int B>
 __device__ __forceinline__ bool place_direct(const DevTable& t, Ctx& c, uint32_t bin, int s, bool hit) {
   if (!cas_slot(t.slots + (uint64_t)bin * B + s, EMPTY, c.krec)) return false;
-  red_relaxed(t.meta + bin, VER_ONE + (hit ? HIT_ONE : 0u));
+  if (hit) red_relaxed(t.meta + bin, HIT_ONE);
   return true;
 }
 
@@ -278,7 +280,7 @@ __device__ __forceinline__ uint64_t* slot_at(const DevTable& t, uint64_t e) {
 // compare-and-swap of the bin's metadata word from the value seen when the
 // bin was viewed, and since that word can come back to an earlier value (its
 // version field wraps), the slot itself is read once more after the claim
-// and must still hold the record the plan saw (check_claimed; a search
+// and must still hold the record the plan saw (reread; a search
 // reads its path's records after claiming them and checks that each belongs
 // to the bin it moves into).  A claimed slot holding a record cannot change
 // until its claim is released, so the writes below need no further check --
@@ -364,7 +366,7 @@ template <int B>
 __device__ __forceinline__ bool claim_twin(const DevTable& t, Ctx& c, uint64_t g, uint32_t y) {
   for (int tries = 0; tries < 4; tries++) {
     View<B> v;
-    load_view<B>(t, y, v);
+    load_view_fast<B>(t, y, v);
     uint32_t dm = dup_mask<B>(v);
     int s = -1;
 #pragma unroll
@@ -388,7 +390,7 @@ __device__ __forceinline__ int take_free(const DevTable& t, Ctx& c, uint32_t bin
   for (int tries = 0;; tries++) {
     if (claim(t, c, bin, v.m, s, K_MOVE, hit, EMPTY)) return ST_OK;
     if (tries == 3) return ST_CONFLICT;
-    load_view<B>(t, bin, v);
+    load_view_fast<B>(t, bin, v);
     c.viewed++;
     c.reviews++;
     if (((free_mask<B>(v) >> s) & 1u) == 0) return ST_CONFLICT;
@@ -427,7 +429,7 @@ __device__ __forceinline__ int take_victim(const DevTable& t, Ctx& c, uint32_t b
   for (int tries = 0;; tries++) {
     if (claim(t, c, bin, v.m, s, K_MOVE, hit, slot_of<B>(v, s))) return ST_OK;
     if (tries == 3) return ST_CONFLICT;
-    load_view<B>(t, bin, v);
+    load_view_fast<B>(t, bin, v);
     c.viewed++;
     c.reviews++;
     uint32_t usable = ~claimed_mask<B>(v) & ~(v.m >> DUP_SHIFT);
@@ -455,11 +457,10 @@ __device__ int insert_random2(const DevTable& t, Ctx& c) {
     c.viewed++;
     s = lowest(free_mask<B>(v1));
     if (s >= 0) return place_direct<B>(t, c, b1, s, false) ? (int)ST_OK : (int)ST_CONFLICT;
-    fence_acquire();  // both metadata words before both bins' slots
-    load_slots<B>(t, b0, v0);
-    load_slots<B>(t, b1, v1);
+    // both full: the views as read serve the walk (unordered metadata and
+    // slots are fine: every move is re-validated after its claim)
   } else {
-    load_view2<B>(t, b0, b1, v0, v1);
+    load_view2_fast<B>(t, b0, b1, v0, v1);
     c.viewed += 2;
     uint32_t f0 = free_mask<B>(v0), f1 = free_mask<B>(v1);
     if (f0 && f1) {
@@ -485,22 +486,46 @@ __device__ int insert_random2(const DevTable& t, Ctx& c) {
   View<B> vx;
   if (idx < n0) { x = b0; vx = v0; s = nth_bit(e0, idx); }
   else { x = b1; vx = v1; s = nth_bit(e1, idx - n0); }
+  // One kick a round trip: the victim's claim goes out together with the
+  // view of the bin it moves to (metadata word and slots, unordered) and the
+  // re-read of the slot the previous kick claimed (reread; that claim has
+  // completed), which is compared once the claim is back.
+  const uint64_t* pend = nullptr;
+  uint64_t pend_v = 0;
   for (;;) {
     if (c.kicks == t.cap) return ST_FAILED;
+    uint64_t victim = slot_of<B>(vx, s);
+    uint32_t xn = other_bin2(t, victim, x);
+    const uint64_t chk = pend ? ld_slot(pend) : 0;
+    View<B> vn;
+    load_view_fast<B>(t, xn, vn);
     int st = take_victim<B>(t, c, x, vx, s, false);
     if (st != ST_OK) return st;
+    if (pend && chk != pend_v) return ST_CONFLICT;
+    if (slot_of<B>(vx, s) != victim) {  // x was viewed again: another record is moving
+      victim = slot_of<B>(vx, s);
+      xn = other_bin2(t, victim, x);
+      load_view_fast<B>(t, xn, vn);
+    }
     c.kicks++;
-    uint64_t victim = slot_of<B>(vx, s);
-    const uint64_t chk = reread<B>(t, x, (uint32_t)s);
-    x = other_bin2(t, victim, x);
-    load_view<B>(t, x, vx);
-    if (chk != victim) return ST_CONFLICT;
+    pend = t.slots + (uint64_t)x * B + s;
+    pend_v = victim;
+    x = xn;
+    vx = vn;
     c.viewed++;
     uint32_t fm = free_mask<B>(vx);
-    if (fm) return take_free<B>(t, c, x, vx, lowest(fm), false);
+    if (fm) {
+      const uint64_t chk_last = ld_slot(pend);
+      const int r = take_free<B>(t, c, x, vx, lowest(fm), false);
+      return (r == ST_OK && chk_last != pend_v) ? (int)ST_CONFLICT : r;
+    }
     if (GHOST) {
       uint32_t dm = dup_mask<B>(vx);
-      if (dm) return take_dup<B>(t, c, x, vx, lowest(dm), false);
+      if (dm) {
+        const uint64_t chk_last = ld_slot(pend);
+        const int r = take_dup<B>(t, c, x, vx, lowest(dm), false);
+        return (r == ST_OK && chk_last != pend_v) ? (int)ST_CONFLICT : r;
+      }
     }
     uint32_t claimed = claimed_mask<B>(vx);
     uint32_t e = FULL & ~claimed & ~(vx.m >> DUP_SHIFT);
@@ -542,14 +567,12 @@ __device__ int insert_queue(const DevTable& t, Ctx& c) {
       int s = lowest(first ? g0 : g1);
       return place_direct<B>(t, c, x, s, true) ? (int)ST_OK : (int)ST_CONFLICT;
     }
-    // both full: the metadata words, then the slots again after them
+    // both full: the metadata words, with the slots as read (unordered is
+    // fine: every move is re-validated after its claim)
     v0.m = ld_relaxed(t.meta + b0);
     v1.m = ld_relaxed(t.meta + b1);
-    fence_acquire();
-    load_slots<B>(t, b0, v0);
-    load_slots<B>(t, b1, v1);
   } else {
-    load_view2<B>(t, b0, b1, v0, v1);
+    load_view2_fast<B>(t, b0, b1, v0, v1);
     c.viewed += 2;
   }
   uint32_t fm0 = free_mask<B>(v0), fm1 = free_mask<B>(v1);
@@ -577,15 +600,24 @@ __device__ int insert_queue(const DevTable& t, Ctx& c) {
     x = first ? b0 : b1;
     vx = first ? v0 : v1;
   }
+  // One kick a round trip: the claim goes out together with the view of
+  // the next bin (metadata word and slots, unordered) and the re-read of the
+  // slot the previous kick claimed (reread; that claim has completed),
+  // compared once the claim is back.
+  const uint64_t* pend = nullptr;
+  uint64_t pend_v = 0;
   for (;;) {
     int tries = 0;
     for (;;) {  // one step at bin x: free slot, duplicate, or victim from hit mod B
       uint32_t h = hit_of(vx.m) % B;
       uint32_t fm = free_mask<B>(vx);
+      const uint64_t chk = pend ? ld_slot(pend) : 0;
       if (fm) {
-        if (claim(t, c, x, vx.m, lowest(fm), K_MOVE, true, EMPTY)) return ST_OK;
+        if (claim(t, c, x, vx.m, lowest(fm), K_MOVE, true, EMPTY))
+          return (pend && chk != pend_v) ? (int)ST_CONFLICT : (int)ST_OK;
       } else if (GHOST && dup_mask<B>(vx)) {
-        return take_dup<B>(t, c, x, vx, first_from<B>(dup_mask<B>(vx), h), true);
+        const int r = take_dup<B>(t, c, x, vx, first_from<B>(dup_mask<B>(vx), h), true);
+        return (r == ST_OK && pend && chk != pend_v) ? (int)ST_CONFLICT : r;
       } else {
         // the victim: the record at slot h mod B, skipping slots another
         // insertion holds; a slot this chain already wrote is taken again
@@ -606,23 +638,21 @@ __device__ int insert_queue(const DevTable& t, Ctx& c) {
         const int jprev = rev ? last_entry_for(c, x, (uint32_t)s) : -1;
         const uint64_t victim = rev ? placed_by(c, jprev) : slot_of<B>(vx, s);
         const uint32_t xn = other_bin2(t, victim, x);
-        // the next bin's metadata word travels with the claim; a fence
-        // then orders it before that bin's slots
-        const uint32_t mn = ld_relaxed(t.meta + xn);
+        View<B> vn;
+        load_view_fast<B>(t, xn, vn);
         if (rev ? claim_again(t, c, x, vx.m, s, jprev, victim) : claim(t, c, x, vx.m, s, K_MOVE, true, victim)) {
+          if (pend && chk != pend_v) return ST_CONFLICT;
           c.kicks++;
-          // a slot the chain holds already carries the plan's record
-          const uint64_t chk = rev ? victim : reread<B>(t, x, (uint32_t)s);
+          // a slot the chain holds already carries the plan's record: no re-read
+          pend = rev ? nullptr : t.slots + (uint64_t)x * B + s;
+          pend_v = victim;
           x = xn;
-          vx.m = mn;
-          fence_acquire();
-          load_slots<B>(t, x, vx);
-          if (chk != victim) return ST_CONFLICT;
+          vx = vn;
           break;
         }
       }
       if (++tries == 4) return ST_CONFLICT;
-      load_view<B>(t, x, vx);
+      load_view_fast<B>(t, x, vx);
       c.viewed++;
       c.reviews++;
     }
@@ -643,7 +673,7 @@ __device__ inline int insert_random_dary(const DevTable& t, Ctx& c) {
   View<1> v[4];
 #pragma unroll
   for (int i = 0; i < 4; i++)
-    if (i < (int)t.d) load_view<1>(t, b[i], v[i]);  // the d loads overlap
+    if (i < (int)t.d) load_view_fast<1>(t, b[i], v[i]);  // the d loads overlap
   for (uint32_t i = 0; i < t.d; i++) {
     c.viewed++;
     if (free_mask<1>(v[i]) && take_free<1>(t, c, b[i], v[i], 0, false) == ST_OK) return ST_OK;
@@ -663,6 +693,13 @@ __device__ inline int insert_random_dary(const DevTable& t, Ctx& c) {
   }
   bool counted = true;  // the first candidates were counted above
   uint32_t holder = NO_BIN;  // the bin whose record is in hand (the last one claimed)
+  // One kick a round trip: the displaced record's other bins are viewed
+  // together with its claim, and the slot the previous kick claimed is read
+  // again (reread) in the same round trip.
+  const uint64_t* pend = nullptr;
+  uint64_t pend_v = 0;
+  uint32_t vb[4];
+  View<1> w[4];
   for (uint32_t waits = 0;;) {
     if (nc == 0 && c.foreign && holder != NO_BIN && waits < 8) {
       // every candidate is held by other insertions, which release their
@@ -670,12 +707,10 @@ __device__ inline int insert_random_dary(const DevTable& t, Ctx& c) {
       // abandon the whole walk (a bounded wait, so no deadlock)
       __nanosleep(256u << waits);
       waits++;
-      uint32_t vb[4];
       bins_of(t, key_of(c.held), vb);
-      View<1> w[4];
 #pragma unroll
       for (int i = 0; i < 4; i++)
-        if (i < (int)t.d && vb[i] != holder) load_view<1>(t, vb[i], w[i]);
+        if (i < (int)t.d && vb[i] != holder) load_view_fast<1>(t, vb[i], w[i]);
       for (uint32_t i = 0; i < t.d; i++) {
         if (vb[i] == holder) continue;
         if (!claimed_mask<1>(w[i])) { cb[nc] = vb[i]; cv[nc] = w[i]; nc++; }
@@ -691,18 +726,25 @@ __device__ inline int insert_random_dary(const DevTable& t, Ctx& c) {
     bool kicked = false, lost = false;
     for (int tries = 0; tries < 4 && !kicked && !lost; tries++) {
       if (tries) {  // lost a race for x: view it again
-        load_view<1>(t, x, vx);
+        load_view_fast<1>(t, x, vx);
         c.viewed++;
         c.reviews++;
       }
       if (claimed_mask<1>(vx)) { lost = true; break; }
+      const uint64_t chk = pend ? ld_slot(pend) : 0;
       if (vx.s[0] == EMPTY) {
-        if (claim(t, c, x, vx.m, 0, K_MOVE, false, EMPTY)) return ST_OK;
+        if (claim(t, c, x, vx.m, 0, K_MOVE, false, EMPTY))
+          return (pend && chk != pend_v) ? (int)ST_CONFLICT : (int)ST_OK;
         continue;
       }
       if (c.kicks == t.cap) return ST_FAILED;
       if (int r = plan_room(t, c)) return r;
+      bins_of(t, key_of(vx.s[0]), vb);
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+        if (i < (int)t.d && vb[i] != x) load_view_fast<1>(t, vb[i], w[i]);
       kicked = claim(t, c, x, vx.m, 0, K_MOVE, false, vx.s[0]);
+      if (kicked && pend && chk != pend_v) return ST_CONFLICT;
     }
     if (!kicked) {
       c.foreign = 1;
@@ -714,14 +756,8 @@ __device__ inline int insert_random_dary(const DevTable& t, Ctx& c) {
     c.kicks++;
     holder = x;
     c.held = vx.s[0];
-    const uint64_t chk = reread<1>(t, x, 0);
-    uint32_t vb[4];
-    bins_of(t, key_of(vx.s[0]), vb);
-    View<1> w[4];
-#pragma unroll
-    for (int i = 0; i < 4; i++)
-      if (i < (int)t.d && vb[i] != x) load_view<1>(t, vb[i], w[i]);
-    if (chk != c.held) return ST_CONFLICT;
+    pend = t.slots + x;
+    pend_v = c.held;
     nc = 0;
     for (uint32_t i = 0; i < t.d; i++) {
       if (vb[i] == x) continue;  // just claimed by this chain
@@ -751,7 +787,7 @@ __device__ inline int insert_rattle(const DevTable& t, Ctx& c) {
     rc = rc < 255 ? rc + 1 : 255;
     View<1> vx;
     const uint64_t chk = pend ? ld_slot(pend) : 0;
-    load_view<1>(t, x, vx);
+    load_view_fast<1>(t, x, vx);
     if (pend) {
       if (chk != pend_v) return ST_CONFLICT;
       pend = nullptr;
@@ -769,7 +805,7 @@ __device__ inline int insert_rattle(const DevTable& t, Ctx& c) {
     bool moved = false, skip = false;
     for (int k = 0; k < 4 && !moved && !skip; k++) {
       if (k) {
-        load_view<1>(t, x, vx);
+        load_view_fast<1>(t, x, vx);
         c.viewed++;
         c.reviews++;
         if (claimed_mask<1>(vx)) {

@@ -342,11 +342,12 @@ __global__ void __launch_bounds__(256, 4) k_insert(DevTable t, const uint32_t* _
   if (t.scratch && !region) usable = false;
   const unsigned long long size_base = load_base;
 
-  // per-thread tallies of one launch (32-bit: a thread handles far fewer
-  // than 2^32 keys or bin views in one launch), flushed into 64-bit counters
-  uint32_t ok = 0, failed = 0, aborted = 0, viewed = 0, kicks = 0, ghosts = 0, dupev = 0, updates = 0;
-  uint32_t reviews = 0, viewed_all = 0;
-  uint32_t aborts = 0, chain_max = 0;
+  // per-thread tallies of the counts every key adds to (32-bit: a thread
+  // handles far fewer than 2^32 keys or bin views in one launch), flushed
+  // into the block's 64-bit counters at the end; the rarer counts go to the
+  // block's counters as they happen, which keeps them out of registers for
+  // the whole loop
+  uint32_t ok = 0, viewed = 0, viewed_all = 0;
   for (;;) {
     uint64_t i = atomicAdd(&s_next, 1ull);
     if (i >= hi) break;
@@ -363,8 +364,7 @@ __global__ void __launch_bounds__(256, 4) k_insert(DevTable t, const uint32_t* _
       DelPlan up;
       int r = update_one<B>(t, key, c.krec, up);
       if (r != 0) {
-        updates += r == 1;
-        aborted += r == 2;
+        atomicAdd(&bc[r == 1 ? C_UPDATES : C_INS_ABORTED], 1ull);
         if (status) status[i] = (uint8_t)(r == 1 ? ST_UPDATED : ST_ABORTED);
         if (viewed_out) viewed_out[i] = 0;
         continue;
@@ -372,6 +372,7 @@ __global__ void __launch_bounds__(256, 4) k_insert(DevTable t, const uint32_t* _
     }
     c.viewed = 0;
     c.reviews = 0;
+    uint32_t aborts = 0;
     // concurrent mode retries a failed attempt (up to three times): other
     // insertions moved records meanwhile, so the next walk or search differs;
     // the serial replay never retries
@@ -379,22 +380,23 @@ __global__ void __launch_bounds__(256, 4) k_insert(DevTable t, const uint32_t* _
                     : (int)ST_ABORTED;
     if (st == ST_OK) {
       ok++;
-      kicks += c.kicks;
-      chain_max = max(chain_max, c.kicks);
+      if (c.kicks) {
+        atomicAdd(&bc[C_KICKS], (unsigned long long)c.kicks);
+        atomicMax(&bc[C_CHAIN_MAX], (unsigned long long)c.kicks);
+      }
       atomicAdd(&h_chain[chain_bucket(c.kicks)], 1u);
-      ghosts += c.ghosts_made;
-      dupev += c.dup_evict;
-    } else if (st == ST_FAILED) {
-      failed++;
+      if (c.ghosts_made) atomicAdd(&bc[C_GHOSTS_MADE], (unsigned long long)c.ghosts_made);
+      if (c.dup_evict) atomicAdd(&bc[C_DUP_EVICT], (unsigned long long)c.dup_evict);
     } else {
-      aborted++;
+      atomicAdd(&bc[st == ST_FAILED ? C_INS_FAILED : C_INS_ABORTED], 1ull);
     }
+    if (aborts) atomicAdd(&bc[C_ABORTS], (unsigned long long)aborts);
+    if (c.reviews) atomicAdd(&bc[C_REVIEWS], (unsigned long long)c.reviews);
     // bins viewed by the attempt that was applied (or failed), and by all
     // attempts including those abandoned after claim conflicts
     uint32_t v_final = c.viewed - c.viewed0;
     viewed += v_final;
     viewed_all += c.viewed;
-    reviews += c.reviews;
     if (status) status[i] = (uint8_t)st;
     if (viewed_out) viewed_out[i] = v_final;
     uint64_t bucket = ((size_base + i) * HIST_BUCKETS) / t.total_slots;
@@ -403,17 +405,8 @@ __global__ void __launch_bounds__(256, 4) k_insert(DevTable t, const uint32_t* _
     atomicAdd(&h_cnt[bucket], 1u);
   }
   flush_counter(&bc[C_INS_OK], ok);
-  flush_counter(&bc[C_INS_FAILED], failed);
-  flush_counter(&bc[C_INS_ABORTED], aborted);
   flush_counter(&bc[C_VIEWED], viewed);
-  flush_counter(&bc[C_KICKS], kicks);
-  flush_counter(&bc[C_ABORTS], aborts);
-  flush_counter(&bc[C_GHOSTS_MADE], ghosts);
-  flush_counter(&bc[C_DUP_EVICT], dupev);
-  flush_counter(&bc[C_REVIEWS], reviews);
   flush_counter(&bc[C_VIEWED_ALL], viewed_all);
-  flush_counter(&bc[C_UPDATES], updates);
-  if (chain_max) atomicMax(&bc[C_CHAIN_MAX], (unsigned long long)chain_max);
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int k = 0; k < C_N; k++) {

@@ -154,7 +154,7 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
     load_slots<B>(t, b0, v0);
     load_slots<B>(t, b1, v1);
   } else {
-    load_view2<B>(t, b0, b1, v0, v1);
+    load_view2_fast<B>(t, b0, b1, v0, v1);
     c.viewed += 2;
   }
   uint32_t f0 = free_mask<B>(v0), f1 = free_mask<B>(v1);
@@ -254,7 +254,7 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
     for (uint32_t i = 0; i < nr; i++) {
       const uint32_t g = rg[i], s = rs[i], y = ry[i];
       View<B> vy;
-      load_view<B>(t, y, vy);
+      load_view_fast<B>(t, y, vy);
       if (claimed_mask<B>(vy)) c.foreign = 1;
       uint32_t fm = free_mask<B>(vy);
       int term = lowest(fm);
@@ -324,7 +324,7 @@ __device__ int insert_search_dary(const DevTable& t, Ctx& c, uint8_t* region) {
   View<1> v[4];
 #pragma unroll
   for (int i = 0; i < 4; i++)
-    if (i < (int)d) load_view<1>(t, b[i], v[i]);  // the d loads overlap
+    if (i < (int)d) load_view_fast<1>(t, b[i], v[i]);  // the d loads overlap
   for (uint32_t i = 0; i < d; i++) {
     c.viewed++;
     if (free_mask<1>(v[i])) return take_free<1>(t, c, b[i], v[i], 0, false);
@@ -405,7 +405,7 @@ __device__ int insert_search_dary(const DevTable& t, Ctx& c, uint8_t* region) {
     for (uint32_t i = 0; i < nr; i++) {
       const uint32_t g = rg[i], y = ry[i];
       View<1> vy;
-      load_view<1>(t, y, vy);
+      load_view_fast<1>(t, y, vy);
       if (claimed_mask<1>(vy)) c.foreign = 1;
       if (!free_mask<1>(vy)) {
         push(y, vy.m, g << 3);

@@ -171,16 +171,22 @@ def test_concurrent_set_semantics_match_oracle(bins, B, d, policy, load):
     assert t.contents() == ref.contents()
     s, os_ = t.stats(), ref.stats()
     assert s["size"] == len(keys) and s["live_ghosts"] == info["ghost_pairs"]
-    # bins viewed per insertion, all attempts counted (abandoned ones and
-    # re-views included): within 10% of the serial oracle at the same load.
-    # d-ary random walks are the exception: their walk lengths are heavy-
-    # tailed, and a long walk that meets other insertions' claims is
-    # abandoned and drawn again, which shortens the tail; the band there is
-    # 25% below to 10% above.
+    # bins viewed per insertion by the attempts that were applied: within
+    # 10% of the serial oracle at the same load.  Counting every attempt
+    # (abandoned ones, re-views, and the larger-budget retry of a search
+    # that ran out of budget) the two-choice policies stay within 10% too.
+    # d-ary walks and searches are heavy-tailed: a long random walk that
+    # meets other insertions' claims is abandoned and drawn again (which
+    # shortens the tail: its applied attempts may view a third fewer bins),
+    # and a search retried with four times the budget adds its views; their
+    # all-attempts band is 25% either way.
     assert s["bins_viewed_all"] >= s["bins_viewed"]
+    applied = s["bins_viewed"] / os_["bins_viewed"]
+    lo_applied = 0.50 if (d > 2 and policy & 0xFF == ck.RANDOM) else 0.90  # restarted walks are shorter
+    assert lo_applied < applied < 1.10, (s["bins_viewed"], os_["bins_viewed"])
     ratio = s["bins_viewed_all"] / os_["bins_viewed"]
-    lo = 0.75 if (d > 2 and policy & 0xFF == ck.RANDOM) else 0.90
-    assert lo < ratio < 1.10, (s["bins_viewed_all"], s["bins_viewed"], os_["bins_viewed"], s["aborts"])
+    lo, hi = (0.75, 1.25) if d > 2 else (0.90, 1.10)
+    assert lo < ratio < hi, (s["bins_viewed_all"], s["bins_viewed"], os_["bins_viewed"], s["aborts"])
     # lookups, 50% present / 50% absent
     probe, expect = inputs.lookup_keys(keys, 1 << 16, 9, 0.5, next_start=nxt)
     v, fnd = t.lookup(ck.as_u32_tensor(probe))
