@@ -481,7 +481,8 @@ __device__ int free_slots(const TxDev& t, const Txn& x, uint32_t bin, const uint
 // start from different slots.  Otherwise (random kicking): a uniformly
 // drawn slot, or the next eligible one after it.  With claim flags the slot
 // is claimed here; a claim lost meanwhile passes the slot over.  -1: none
-// found (-2: the bin could not be viewed).
+// found; -3: none found, but slots other transactions hold claimed were
+// passed over (contention, not a full bin); -2: the bin could not be viewed.
 __device__ int target_slot(const TxDev& t, Txn& x, uint32_t bin, const uint32_t* path, int np, uint64_t& rec,
                            unsigned long long& word) {
   const bool queue = t.flags & CK_TXF_QUEUE;
@@ -489,19 +490,26 @@ __device__ int target_slot(const TxDev& t, Txn& x, uint32_t bin, const uint32_t*
   const uint32_t start = queue ? atomicAdd(t.hit + bin, 1u) % t.B : (uint32_t)(next_draw(x) % t.B);
   BinView v;
   if (!view_bin(t, bin, v)) return -2;
+  bool foreign = false;
   for (int pass = queue ? 0 : 1; pass < 2; pass++) {  // queue: free slots first
     for (uint32_t k = 0; k < t.B; k++) {
       const uint32_t s = (start + k) % t.B;
       const uint32_t idx = bin * t.B + s;
       if (pass == 0 && v.rec[s] != EMPTY) continue;
-      if (!eligible(t, x, idx, v.w[s]) || on_path(path, np, idx)) continue;
-      if (claim && !claim_slot(t, idx, v.w[s])) continue;
+      if (!eligible(t, x, idx, v.w[s]) || on_path(path, np, idx)) {
+        if (claim && (v.w[s] & W_CLAIM) && !on_path(path, np, idx) && hs_find(x, idx) < 0) foreign = true;
+        continue;
+      }
+      if (claim && !claim_slot(t, idx, v.w[s])) {
+        foreign = true;
+        continue;
+      }
       rec = v.rec[s];
       word = v.w[s] | (claim ? W_CLAIM : 0ull);
       return (int)idx;
     }
   }
-  return -1;
+  return foreign ? -3 : -1;
 }
 
 // A system transaction moving record r from slot src to the empty slot dst
@@ -582,7 +590,7 @@ __device__ int plan_insert(const TxDev& t, Txn& x, uint64_t rec, uint32_t b0, ui
     } else {
       s = target_slot(t, x, bin, path, 0, occ, sw);
       if (s < 0) {
-        x.cause = s == -2 ? TXS_ABORT_LOCK : TXS_ABORT_CHAIN;
+        x.cause = s == -2 ? TXS_ABORT_LOCK : s == -3 ? TXS_ABORT_CLAIMED : TXS_ABORT_CHAIN;
         return 1;
       }
     }
@@ -625,7 +633,7 @@ __device__ int plan_insert(const TxDev& t, Txn& x, uint64_t rec, uint32_t b0, ui
       if (ns < 0) {
         ns = target_slot(t, x, y, path, np, nocc, nw);
         if (ns < 0) {
-          x.cause = ns == -2 ? TXS_ABORT_LOCK : TXS_ABORT_CHAIN;
+          x.cause = ns == -2 ? TXS_ABORT_LOCK : ns == -3 ? TXS_ABORT_CLAIMED : TXS_ABORT_CHAIN;
           result = 1;
           break;
         }
