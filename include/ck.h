@@ -84,6 +84,12 @@ extern "C" {
                                    time lets their bins be fetched together; every bin of a
                                    round counts as viewed, and the first with room, in
                                    candidate order, ends the search. */
+#define CK_PARAM_MAX_INFLIGHT 35 /* insertions one insert launch keeps in flight at most
+                                    (0, the default: as many threads as fit on the GPU; else
+                                    whole blocks, one at least).  Claim conflicts grow with the
+                                    share of a table's slots in flight, so a small table can
+                                    fill faster with fewer insertions at once, each thread
+                                    taking more keys. */
 #define CK_PARAM_HASH_FAMILY 33 /* 0 (default): h_i = fmix32(k ^ seed_i); 1: decorrelated
                                    h_i = fmix32(fmix32(k + seed_i) ^ (seed_i * 0x27D4EB2F)).
                                    Set before the first insertion. */

@@ -24,6 +24,7 @@ struct ck_table {
   uint32_t overlap;      // insert launches may overlap their predecessor
   uint32_t block;
   uint32_t policy_code;  // as passed by the caller (policy | ghost flag)
+  uint64_t max_inflight; // insertions in flight per insert launch at most (0: as many as fit)
 };
 
 namespace {
@@ -158,6 +159,7 @@ int init_table(ck_table* t, void* buf, size_t bytes, bool owns, uint64_t bins, u
   t->overlap = 1;
   t->load_base = 0;
   t->policy_code = policy;
+  t->max_inflight = 0;
   if (cudaGetDevice(&t->device) != cudaSuccess) return CK_ECUDA;
   if (cudaDeviceGetAttribute(&t->sm_count, cudaDevAttrMultiProcessorCount, t->device) != cudaSuccess)
     return CK_ECUDA;
@@ -309,6 +311,10 @@ int ck_set_param(ck_table* t, int key, int64_t value) {
       if (value < 1 || value > 8) return CK_EINVAL;
       d.spawn_k = (uint32_t)value;
       return CK_OK;
+    case CK_PARAM_MAX_INFLIGHT:
+      if (value < 0 || value > (1ll << 40)) return CK_EINVAL;
+      t->max_inflight = (uint64_t)value;
+      return CK_OK;
     case CK_PARAM_HASH_FAMILY:
       if (value != 0 && value != 1) return CK_EINVAL;
       d.hash_family = (uint32_t)value;
@@ -331,7 +337,8 @@ int ck_insert_batch_ex(ck_table* t, const uint32_t* d_keys, const uint32_t* d_va
   if (flags & ~(uint32_t)(CK_INS_SERIAL | CK_INS_UPSERT)) return CK_EINVAL;
   InsertFn fn = pick_insert(t);
   if (!fn) return CK_ENOTSUP;
-  const InsertLaunch l{&t->dt, t->block, t->sm_count, t->overlap != 0, t->load_base, ~0ull};
+  const InsertLaunch l{&t->dt, t->block, t->sm_count, t->overlap != 0, t->load_base,
+                       t->max_inflight ? t->max_inflight : ~0ull};
   cudaError_t e = fn(l, d_keys, d_vals, n, d_status, d_viewed, (flags & CK_INS_SERIAL) != 0,
                      (flags & CK_INS_UPSERT) ? 1u : 0u, S(stream));
   t->last = S(stream);
