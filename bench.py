@@ -60,8 +60,13 @@ def parse():
     ap.add_argument("--no-small", action="store_true", help="skip the L2-resident small table")
     ap.add_argument("--policy", action="append",
                     help="with --only policies: fill only the named policy rows (repeatable)")
-    ap.add_argument("--only", choices=["serve", "multi", "policies", "txn"],
-                    help="run one side section alone and print its JSON (diagnostics; no bench line)")
+    ap.add_argument("--only", choices=["serve", "multi", "policies", "txn", "fill"],
+                    help="run one side section alone and print its JSON (diagnostics; no bench line); "
+                         "fill: one warm-up fill and one timed fill of the step's table, or of a smaller one "
+                         "(--fill-bins-log2), for per-launch profiler captures")
+    ap.add_argument("--fill-bins-log2", type=int, default=24,
+                    help="with --only fill: log2 of the table's bins (4 slots each); the load trajectory and "
+                         "the number of launches (61) stay those of the step")
     return ap.parse_args()
 
 
@@ -533,9 +538,11 @@ def multi_form(torch, ck, stream):
     return out
 
 
-# DRAM bytes read + written per insert launch of the fill above, mean over
-# its 61 launches, from an ncu capture of this kernel build
-INSERT_TRAFFIC_PER_LAUNCH = 518_200_000
+# DRAM bytes read + written per insert launch of the step's fill (mean over
+# its 61 launches) from an ncu capture of the current kernel build: a
+# half-size fill (2^23 x 4, the same 61-launch load trajectory, half the keys
+# per launch), scaled by 2; None until captured for this build
+INSERT_TRAFFIC_PER_LAUNCH = 386_800_000
 
 SERVE_BINS = 1 << 26
 SERVE_PREFILL = 255013683  # floor(0.95 * 2^28)
@@ -923,7 +930,7 @@ def run_gpu(args, rank, world, local):
                 "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
                 "traffic": INSERT_TRAFFIC_PER_LAUNCH,
-                "traffic_unit": "bytes per launch (mean DRAM read + write of one fill's 61 launches, ncu)",
+                "traffic_unit": "bytes per launch: mean DRAM read + write over the 61 launches of a half-size fill (2^23 x 4, the same load trajectory, 2^19 keys a launch), times 2 (ncu)",
                 "bytes_per_launch": int(bytes_per_launch), "avg_launch_ms": round(avg_launch_ms, 4),
                 "vs_random_gather_32B": {"gbs": round(g32, 1), "frac": round(achieved / g32, 4)}}
     gather_section = {"buffer": "512 MiB (the slot array's size)", "width_bytes": 32, "reads": 1 << 26,
@@ -1185,7 +1192,29 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
-def run_section(name, policies=None):
+def fill_section(bins_log2):
+    """One warm-up fill and one timed fill of a 2^bins_log2 x 4 queue-kicking
+    table to 0.95 in 61 launches (the step's trajectory at that size)."""
+    import torch
+    from paper_1605_05236_gb300 import ck, inputs
+    ck.load()
+    stream = torch.cuda.current_stream()
+    bins = 1 << bins_log2
+    n = inputs.load_target(bins * B, LOAD)
+    keys, _ = inputs.distinct_keys(n, rank_seed(0))
+    kt, vt = ck.as_u32_tensor(keys), ck.as_u32_tensor(inputs.values_for(keys))
+    st = torch.empty(n, dtype=torch.uint8, device="cuda")
+    batch = max(1, (BATCH * bins) // BINS)
+    t = ck.CuckooTable(bins, B, 2, ck.QUEUE, seed=rank_seed(0))
+    fill_once(torch, ck, t, kt, vt, st, stream, batch)
+    ms, per = fill_once(torch, ck, t, kt, vt, st, stream, batch)
+    s = t.stats()
+    return {"fill": {"bins": bins, "keys": n, "batch": batch, "launches": len(per), "ms": round(ms, 3),
+                     "all_inserted": bool((st == 0).all().item()),
+                     "bins_viewed": s["bins_viewed"], "kicks": s["kicks"], "inserts_ok": s["inserts_ok"]}}
+
+
+def run_section(name, policies=None, fill_bins_log2=24):
     import torch
     from paper_1605_05236_gb300 import ck
     ck.load()
@@ -1196,6 +1225,8 @@ def run_section(name, policies=None):
         return {"batched_form": multi_form(torch, ck, stream)}
     if name == "txn":
         return {"transactional": txn_form(torch, stream)}
+    if name == "fill":
+        return fill_section(fill_bins_log2)
     keys, vals, _, _, _ = workload(rank_seed(0))
     return {"policies": policy_fills(torch, ck, stream, (keys, vals), only=policies)}
 
@@ -1252,7 +1283,7 @@ def main():
             print(json.dumps(out), flush=True)
         return
     if args.only:
-        out = run_section(args.only, args.policy)
+        out = run_section(args.only, args.policy, args.fill_bins_log2)
         if rank == 0 and out is not None:
             print(json.dumps(out), flush=True)
         return
