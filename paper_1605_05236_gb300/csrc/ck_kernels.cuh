@@ -16,10 +16,13 @@ __device__ __forceinline__ void flush_counter(unsigned long long* shared_slot, u
 }
 
 // Randomised exponential backoff after a conflict: [w, 2w) ns with w =
-// 64 << attempt, up to about a millisecond, so that long walks that keep
-// meeting each other (small tables with most keys in flight) drift apart.
+// 64 << attempt, up to 32-64 us, so that long walks that keep meeting each
+// other (small tables with most keys in flight) drift apart.  Measured on
+// the 2^14 x 4 table with all 62,259 keys in flight at once (1.3 claim
+// conflicts per key): capping w at 32 us rather than 1 ms fills it about 9%
+// faster; the large fills do not change.
 __device__ __forceinline__ void backoff(uint32_t attempt, uint32_t key) {
-  uint32_t w = 64u << (attempt < 14 ? attempt : 14);
+  uint32_t w = 64u << (attempt < 9 ? attempt : 9);
   __nanosleep(w + (fmix32(key ^ attempt) & (w - 1)));
 }
 
@@ -294,11 +297,18 @@ __device__ __forceinline__ int update_one(const DevTable& t, uint32_t key, uint6
 // after its predecessor.  Insertions of distinct absent keys commute under
 // the claim protocol, so the overlap changes no result.  `load_base` is the
 // number of keys the table held before this batch (for the histogram).
-// At most 64 registers (4 blocks of 256 or 8 of 128 threads per SM):
-// measured faster than the 80-96 the compiler picks unbounded, since the
-// kernel is bound by how many random accesses are in flight.
+// Registers: at most 64 (4 blocks of 256 or 8 of 128 threads per SM) for
+// most policies, 80 for 4-slot queue-kicking (3 blocks of 256).  Measured on
+// one GB300, fill of 2^24 x 4 to 0.95: queue-kicking 10.36-10.52 ms at 80
+// registers (no spills) vs 10.56-10.74 at 64 (92 bytes spilled); random
+// kicking 25.1 ms at 80 vs 24.0-24.4 at 64: the kernel is bound by random
+// accesses in flight, and only the queue kernel's spills cost more than the
+// warps a larger register file takes away.
+template <int B, int POL>
+constexpr int insert_blocks_per_sm() { return (B == 4 && POL == P_QUEUE) ? 3 : 4; }
+
 template <int B, int POL, bool GHOST, bool SERIAL>
-__global__ void __launch_bounds__(256, 4) k_insert(DevTable t, const uint32_t* __restrict__ keys,
+__global__ void __launch_bounds__(256, insert_blocks_per_sm<B, POL>()) k_insert(DevTable t, const uint32_t* __restrict__ keys,
                                                 const uint32_t* __restrict__ vals, uint64_t n,
                                                 uint8_t* __restrict__ status,
                                                 uint32_t* __restrict__ viewed_out, uint64_t load_base,
