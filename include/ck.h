@@ -64,7 +64,7 @@ extern "C" {
 
 /* ---- runtime parameters for ck_set_param ---- */
 #define CK_PARAM_CHAIN_CAP 1     /* kick-outs (walks), tries (rattle), bins viewed (search); default 500 */
-#define CK_PARAM_MAX_RETRIES 2   /* claim-conflict retries per key; default 64 */
+#define CK_PARAM_MAX_RETRIES 2   /* attempts per key after claim conflicts; default 1024 */
 #define CK_PARAM_RNG_SEED 3      /* seed of the counter-based kick-out draws */
 #define CK_PARAM_HASH_SEED0 10   /* + i for seed_i, i < d (defaults 0x9E3779B9, 0x85EBCA6B, 0xC2B2AE35, 0x27D4EB2F) */
 #define CK_PARAM_BLOCK 20        /* threads per block of the insert kernels: 32, 64, 128 or 256;

@@ -38,7 +38,8 @@ constexpr int LONG_CHAIN = 4104;  // plan entries of a scratch-backed plan (walk
 constexpr int LONG_REGION = 65792;  // bytes of one scratch plan (16 * LONG_CHAIN, 256-aligned)
 constexpr int MAX_GROUPS = 512;   // bins a search can view (budget <= MAX_GROUPS)
 constexpr int VISITED_SLOTS = 1024;
-constexpr int SLAB = 256;         // search regions per slab (one slab per block, blockDim <= SLAB)
+constexpr int SLAB = 64;          // search regions per slab (a block holds ceil(blockDim / SLAB) slabs)
+constexpr int SLABS_PER_BLOCK = 4; // blockDim <= 256
 
 constexpr uint32_t DUP_SHIFT = 8;
 constexpr uint32_t SPAWN_SHIFT = 16;

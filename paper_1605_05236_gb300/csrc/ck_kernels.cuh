@@ -41,24 +41,28 @@ __device__ __forceinline__ int attempt_insert(const DevTable& t, Ctx& c, uint8_t
   }
 }
 
-// A block's slab of search scratch: SLAB consecutive per-thread regions.
-// Taken at block start and returned at block end, so blocks of overlapping
-// launches never share a region.  A block of the next launch may wait for
-// a slab while the previous launch drains; the wait is bounded (about 10 ms),
-// after which the block reports its keys as aborted.
-__device__ __forceinline__ int acquire_slab(const DevTable& t) {
-  uint32_t n_slabs = t.n_searchers / SLAB;
-  if (n_slabs == 0) return -1;
+// A block's search scratch: ceil(blockDim / SLAB) slabs of SLAB consecutive
+// per-thread regions, taken together at block start (all or none: a block
+// never waits while holding a slab, so blocks of overlapping launches cannot
+// hold each other up) and returned at block end.  A block of the next launch
+// may wait for slabs while the previous launch drains; the wait is bounded
+// (about 10 ms), after which the block reports its keys as aborted.
+__device__ __forceinline__ bool acquire_slabs(const DevTable& t, int* out, int need) {
+  const uint32_t n_slabs = t.n_searchers / SLAB;
+  if (n_slabs < (uint32_t)need) return false;
   for (uint32_t round = 0; round < 4096; round++) {
-    uint32_t start = (blockIdx.x + round * 7919u) % n_slabs;
-    for (uint32_t k = 0; k < n_slabs; k++) {
+    int got = 0;
+    uint32_t start = (blockIdx.x * (uint32_t)need + round * 7919u) % n_slabs;
+    for (uint32_t k = 0; k < n_slabs && got < need; k++) {
       uint32_t r = start + k;
       if (r >= n_slabs) r -= n_slabs;
-      if (*(volatile uint32_t*)(t.slab_busy + r) == 0 && atomicCAS(t.slab_busy + r, 0u, 1u) == 0u) return (int)r;
+      if (*(volatile uint32_t*)(t.slab_busy + r) == 0 && atomicCAS(t.slab_busy + r, 0u, 1u) == 0u) out[got++] = (int)r;
     }
+    if (got == need) return true;
+    for (int j = 0; j < got; j++) atomicExch(t.slab_busy + out[j], 0u);
     __nanosleep(2000);
   }
-  return -1;
+  return false;
 }
 
 // One insertion with bounded retries after claim conflicts.  A chain that
@@ -319,7 +323,7 @@ __global__ void __launch_bounds__(256, insert_blocks_per_sm<B, POL>()) k_insert(
   __shared__ unsigned int h_chain[CHAIN_BUCKETS];
   __shared__ unsigned long long bc[C_N];
   __shared__ unsigned long long s_next;  // next key of this block's range
-  __shared__ int s_slab, s_long;
+  __shared__ int s_slab[SLABS_PER_BLOCK], s_long;
   for (int i = threadIdx.x; i < HIST_BUCKETS; i += blockDim.x) h_views[i] = h_cnt[i] = 0;
   for (int i = threadIdx.x; i < CHAIN_BUCKETS; i += blockDim.x) h_chain[i] = 0;
   for (int i = threadIdx.x; i < C_N; i += blockDim.x) bc[i] = 0;
@@ -330,7 +334,8 @@ __global__ void __launch_bounds__(256, insert_blocks_per_sm<B, POL>()) k_insert(
   const uint64_t lo = min(n, (uint64_t)blockIdx.x * per), hi = min(n, lo + per);
   if (threadIdx.x == 0) {
     s_next = lo;
-    s_slab = t.scratch ? acquire_slab(t) : -1;
+    const int need = (int)((blockDim.x + SLAB - 1) / SLAB);
+    if (!t.scratch || !acquire_slabs(t, s_slab, need)) s_slab[0] = -1;
     s_long = SERIAL ? acquire_long(t, 0) : -1;
   }
   __syncthreads();
@@ -347,8 +352,9 @@ __global__ void __launch_bounds__(256, insert_blocks_per_sm<B, POL>()) k_insert(
       usable = false;
     }
   }
-  uint8_t* region = s_slab >= 0 ? t.scratch + ((uint64_t)s_slab * SLAB + threadIdx.x) * SEARCH_REGION
-                                : nullptr;
+  uint8_t* region = s_slab[0] >= 0 ? t.scratch + ((uint64_t)s_slab[threadIdx.x / SLAB] * SLAB + threadIdx.x % SLAB) *
+                                                   SEARCH_REGION
+                                   : nullptr;
   if (t.scratch && !region) usable = false;
   const unsigned long long size_base = load_base;
 
@@ -439,7 +445,10 @@ __global__ void __launch_bounds__(256, insert_blocks_per_sm<B, POL>()) k_insert(
   for (int i = threadIdx.x; i < CHAIN_BUCKETS; i += blockDim.x)
     if (h_chain[i]) atomicAdd(t.counters + CHAIN_HIST + i, (unsigned long long)h_chain[i]);
   if (threadIdx.x == 0) {
-    if (s_slab >= 0) { __threadfence(); atomicExch(t.slab_busy + s_slab, 0u); }
+    if (s_slab[0] >= 0) {
+      __threadfence();
+      for (int j = 0; j < (int)((blockDim.x + SLAB - 1) / SLAB); j++) atomicExch(t.slab_busy + s_slab[j], 0u);
+    }
     if (s_long >= 0) release_long(t, s_long);
   }
   asm volatile("griddepcontrol.wait;" ::: "memory");

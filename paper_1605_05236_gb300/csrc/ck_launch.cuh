@@ -54,7 +54,7 @@ cudaError_t launch_insert(const InsertLaunch& l, const uint32_t* keys, const uin
   uint64_t by_threads = l.max_threads / block;  // insertions in flight at once
   if (grid > by_threads) grid = by_threads > 0 ? by_threads : 1;
   if (dt.scratch) {
-    uint64_t cap_blocks = dt.n_searchers / SLAB;
+    uint64_t cap_blocks = (dt.n_searchers / SLAB) / ((block + SLAB - 1) / SLAB);
     if (grid > cap_blocks) grid = cap_blocks;
   }
   if (grid > 0x7FFFFFFFull) grid = 0x7FFFFFFFull;

@@ -139,7 +139,7 @@ int init_table(ck_table* t, void* buf, size_t bytes, bool owns, uint64_t bins, u
   dt.policy = policy & 0xFF;
   dt.ghost = (policy & CK_GHOST) ? 1 : 0;
   dt.cap = 500;
-  dt.max_retries = 64;
+  dt.max_retries = 1024;
   dt.ordered_writes = 0;  // see CK_PARAM_ORDERED_WRITES
   dt.spawn_k = 1;
   dt.tie_resident = 0;

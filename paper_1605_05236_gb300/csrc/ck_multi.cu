@@ -381,7 +381,7 @@ int ck_multi_create_on(ck_multi** out, void* dev_buf, size_t bytes, const ck_mul
     t.policy = pol;
     t.ghost = (policy & CK_GHOST) ? 1 : 0;
     t.cap = m->cap;
-    t.max_retries = 64;
+    t.max_retries = 1024;
     t.ordered_writes = 0;
     t.spawn_k = 1;
     t.n_searchers = 0;
