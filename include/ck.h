@@ -241,8 +241,8 @@ const char *ck_strerror(int code);
  * ck_insert_batch (the key -> value map it leaves is the one ck_insert_batch
  * leaves for the same keys; the slot layout may differ, as between any two
  * concurrent runs), but the per-search scratch of breadth-first and sorted search comes from a fixed
- * array compiled into libck.so (CK_NOALLOC_MAX_KEYS regions of 16,400 bytes,
- * 8.0 MiB, in the memory of every GPU that loads the library, kept until the
+ * array compiled into libck.so (CK_NOALLOC_MAX_KEYS regions of 16,528 bytes,
+ * 8.1 MiB, in the memory of every GPU that loads the library, kept until the
  * process exits), one region per key, and the call allocates nothing.
  *   - n > CK_NOALLOC_MAX_KEYS: returns CK_EINVAL and launches nothing.
  *   - The first call on a device looks up the array's device address

@@ -107,7 +107,7 @@ __device__ __forceinline__ int insert_one(const DevTable& t, Ctx& c, uint8_t* re
       if (region && c.big_id < 0 && (POL == P_BFS || POL == P_SORTED || POL == P_HYBRID)) {
         c.big_id = acquire_long(t, c.key ^ 0x5bd1e995u);
         if (c.big_id >= 0) {
-          uint64_t* vis = reinterpret_cast<uint64_t*>(t.long_scratch + (uint64_t)c.big_id * LONG_REGION + 16 +
+          uint64_t* vis = reinterpret_cast<uint64_t*>(t.long_scratch + (uint64_t)c.big_id * LONG_REGION + SEARCH_HDR +
                                                       BIG_GROUPS * sizeof(Group));
           for (int i = 0; i < BIG_VISITED; i++) vis[i] = 0;  // the region held a plan: no stale tags
         }

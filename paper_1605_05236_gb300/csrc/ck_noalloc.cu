@@ -13,7 +13,7 @@
 // first call on a device looks up the array's device address; that first
 // call should come before any stream capture.
 //
-// The array: NOALLOC_REGIONS = 512 search regions of 16,400 bytes, 8.0 MiB in
+// The array: NOALLOC_REGIONS = 512 search regions of 16,528 bytes, 8.1 MiB in
 // all, in device memory of every GPU that loads the library, held until the
 // process exits.  One region per key, so a call takes at most 512 keys.
 #include <cuda_runtime.h>

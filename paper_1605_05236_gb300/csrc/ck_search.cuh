@@ -23,10 +23,13 @@
 // record, read after its claim, that does not belong to the bin the path
 // moves it into (the word came back to its viewed value meanwhile).
 //
-// Per-searcher scratch (global memory, SEARCH_REGION bytes): a 16-byte
-// header holding a generation counter, MAX_GROUPS group records, and an
-// open-addressed visited set tagged with the generation (cleared only when
-// the generation wraps).  In concurrent mode a search that spent its budget
+// Per-searcher scratch (global memory, SEARCH_REGION bytes): a header
+// holding a generation counter and the bucket queues that give sorted
+// search and the hybrid their next candidate in constant time, MAX_GROUPS
+// group records, and an open-addressed visited set tagged with the
+// generation (cleared only when the generation wraps).  The d-ary BFS
+// keeps the record of the group it spawns from, with its bins and their
+// visited tests, in registers (GroupCache).  In concurrent mode a search that spent its budget
 // without meeting another insertion's claim is retried with four times the
 // budget in a larger space borrowed from the table's scratch plans
 // (search_space): the layout concurrent filling produces differs from the
@@ -40,21 +43,27 @@ namespace ck {
 struct Group {
   uint32_t bin;
   uint32_t meta;    // metadata word as viewed (updated by our own spawn increments)
-  uint32_t parent;  // (group << 3) | slot of the record that led here; ~0u at a root
+  uint16_t parent;  // (group << 3) | slot of the record that led here; NO_PARENT at a root
+  uint16_t link;    // sorted search, hybrid: the next group in the same bucket
   uint8_t next;     // next slot to pop
   uint8_t stale;    // the bin changed under us: a path through it aborts
   uint16_t key;     // sort key: spawn count when viewed (hybrid: depth * 16 + that count)
 };
 static_assert(sizeof(Group) == 16, "group record is 16 bytes");
+constexpr uint32_t NO_PARENT = 0xFFFFu;
 
-constexpr size_t SEARCH_REGION = 16 + MAX_GROUPS * sizeof(Group) + VISITED_SLOTS * 8;
+// Region header: the generation word, then (sorted search, hybrid) the
+// bucket queues of candidate groups, 32 heads and 32 tails of 16 bits.
+constexpr size_t SEARCH_HDR = 16 + 64 * sizeof(uint16_t);
+constexpr size_t SEARCH_REGION = SEARCH_HDR + MAX_GROUPS * sizeof(Group) + VISITED_SLOTS * 8;
 
 // A larger search space for the retry of a search that ran out of budget in
 // concurrent mode: a scratch plan region (LONG_REGION bytes) holds the
 // header, BIG_GROUPS group records and a visited set of BIG_VISITED slots.
 constexpr int BIG_GROUPS = 2048;
 constexpr int BIG_VISITED = 4096;
-static_assert(16 + BIG_GROUPS * 16 + BIG_VISITED * 8 <= LONG_REGION, "a big search fits a scratch plan region");
+static_assert(SEARCH_HDR + BIG_GROUPS * 16 + BIG_VISITED * 8 <= LONG_REGION, "a big search fits a scratch plan region");
+static_assert(((BIG_GROUPS - 1) << 3 | 7) < NO_PARENT, "a parent reference fits 16 bits");
 static_assert((1 << 10) == VISITED_SLOTS && (1 << 12) == BIG_VISITED, "visited sets are powers of two");
 
 // Where one search keeps its state, and how much it may use.
@@ -75,15 +84,15 @@ __device__ __forceinline__ SearchSpace search_space(const DevTable& t, const Ctx
   if (c.big_id >= 0) {
     uint8_t* r = t.long_scratch + (uint64_t)c.big_id * LONG_REGION;
     s.hdr = reinterpret_cast<uint32_t*>(r);
-    s.G = reinterpret_cast<Group*>(r + 16);
-    s.vis = reinterpret_cast<uint64_t*>(r + 16 + BIG_GROUPS * sizeof(Group));
+    s.G = reinterpret_cast<Group*>(r + SEARCH_HDR);
+    s.vis = reinterpret_cast<uint64_t*>(r + SEARCH_HDR + BIG_GROUPS * sizeof(Group));
     s.max_groups = BIG_GROUPS;
     s.vis_bits = 12;
     s.budget = min(4u * t.cap, (uint32_t)BIG_GROUPS - 8u);
   } else {
     s.hdr = reinterpret_cast<uint32_t*>(region);
-    s.G = reinterpret_cast<Group*>(region + 16);
-    s.vis = reinterpret_cast<uint64_t*>(region + 16 + MAX_GROUPS * sizeof(Group));
+    s.G = reinterpret_cast<Group*>(region + SEARCH_HDR);
+    s.vis = reinterpret_cast<uint64_t*>(region + SEARCH_HDR + MAX_GROUPS * sizeof(Group));
     s.max_groups = MAX_GROUPS;
     s.vis_bits = 10;
     s.budget = t.cap;
@@ -135,6 +144,118 @@ __device__ __forceinline__ bool vis_has(const uint64_t* vis, uint32_t bits, uint
   }
 }
 
+// vis_has, given the entry at the bin's hash position already loaded (so
+// the probes for a group's records overlap).
+__device__ __forceinline__ bool vis_has_from(const uint64_t* vis, uint32_t bits, uint32_t gen, uint32_t bin,
+                                             uint64_t e) {
+  const uint64_t tag = ((uint64_t)gen << 32) | bin;
+  for (uint32_t h = vis_hash(bin, bits);;) {
+    if (e == tag) return true;
+    if ((uint32_t)(e >> 32) != gen) return false;
+    h = (h + 1) & ((1u << bits) - 1);
+    e = vis[h];
+  }
+}
+
+// a[s] for s known only at run time, kept in registers (a chain of selects)
+template <int N>
+__device__ __forceinline__ uint32_t pick(const uint32_t (&a)[N], uint32_t s) {
+  uint32_t r = a[0];
+#pragma unroll
+  for (int q = 1; q < N; q++) r = (s == (uint32_t)q) ? a[q] : r;
+  return r;
+}
+
+// The group a search spawns from: its records' next bins and which of them
+// may spawn, taken when the search starts popping the group (again after it
+// popped another).  A two-choice group's bin is read with one vector load
+// and each record's other bin probed in the visited set, the probes
+// overlapping; a d-ary group's record gives its d bins.  `ok` bit s: record
+// s is present and its bin y[s] was unvisited at that point.  Until the
+// search pops another group, the only bins it marks visited are those its
+// spawns from this group view (`spawned`), so ok and spawned together give
+// exactly the visited test the search makes spawn by spawn.
+template <int N>
+struct GroupCache {
+  uint32_t g;  // group index (~0u: none yet)
+  uint32_t bin, meta, next;
+  uint32_t y[N];
+  uint32_t ok, spawned;
+};
+
+// Was y viewed by a spawn from the cached group since it was taken?
+template <int N>
+__device__ __forceinline__ bool spawned_to(const GroupCache<N>& k, uint32_t y) {
+  bool hit = false;
+#pragma unroll
+  for (int q = 0; q < N; q++) hit |= ((k.spawned >> q) & 1u) && k.y[q] == y;
+  return hit;
+}
+
+__device__ __forceinline__ void take_group_dary(const DevTable& t, const Group* G, uint32_t g, const uint64_t* vis,
+                                                uint32_t vb, uint32_t gen, GroupCache<4>& k) {
+  const Group gr = G[g];
+  k.g = g;
+  k.bin = gr.bin;
+  k.meta = gr.meta;
+  k.next = gr.next;
+  k.spawned = 0;
+  k.ok = 0;
+  const uint64_t rec = ld_slot(t.slots + gr.bin);
+  if (rec == EMPTY) return;
+  bins_of(t, key_of(rec), k.y);
+  uint64_t e[4];
+#pragma unroll
+  for (int j = 0; j < 4; j++) e[j] = j < (int)t.d && k.y[j] != gr.bin ? vis[vis_hash(k.y[j], vb)] : 0;
+#pragma unroll
+  for (int j = 0; j < 4; j++)
+    if (j < (int)t.d && k.y[j] != gr.bin && !vis_has_from(vis, vb, gen, k.y[j], e[j])) k.ok |= 1u << j;
+}
+
+// Bucket queues of candidate groups for sorted search and the hybrid.  A
+// group's key never changes (the spawn count of its bin when viewed; the
+// hybrid adds 16 x its depth), so the candidate with the smallest key,
+// oldest first among equals, is the head of the lowest non-empty bucket,
+// each bucket a list in push order.  Sorted search: bucket = key (0-15).
+// Hybrid: depth-major order means only two depths have candidates at once
+// (the one being spawned from and the next), so bucket = 16 x (depth & 1) +
+// spawn count, and the search looks at the half of its current depth
+// first.  `mask` bit b: bucket b holds a group.
+struct Buckets {
+  uint16_t* q;  // q[b]: head of bucket b, q[32 + b]: its tail
+  uint32_t mask;
+  uint32_t depth;  // hybrid: the depth being spawned from
+};
+
+__device__ __forceinline__ uint32_t bucket_of(int order, uint32_t key) {
+  return order == P_HYBRID ? ((key >> 4) & 1u) * 16u + (key & 15u) : key;
+}
+
+__device__ __forceinline__ void bucket_push(Buckets& bq, Group* G, uint32_t b, uint32_t g) {
+  if ((bq.mask >> b) & 1u) G[bq.q[32 + b]].link = (uint16_t)g;
+  else bq.q[b] = (uint16_t)g;
+  bq.q[32 + b] = (uint16_t)g;
+  bq.mask |= 1u << b;
+}
+
+// The bucket to spawn from, or -1 when no candidate is left.
+__device__ __forceinline__ int bucket_min(int order, Buckets& bq) {
+  if (bq.mask == 0) return -1;
+  if (order != P_HYBRID) return __ffs(bq.mask) - 1;
+  uint32_t half = (bq.depth & 1u) ? (bq.mask >> 16) : (bq.mask & 0xFFFFu);
+  if (half == 0) {  // this depth is exhausted: the next one
+    bq.depth++;
+    half = (bq.depth & 1u) ? (bq.mask >> 16) : (bq.mask & 0xFFFFu);
+  }
+  return (int)((bq.depth & 1u) * 16u) + __ffs(half) - 1;
+}
+
+// Group g, the head of bucket b, has no record left to spawn.
+__device__ __forceinline__ void bucket_pop(Buckets& bq, const Group* G, uint32_t b, uint32_t g) {
+  if (bq.q[32 + b] == (uint16_t)g) bq.mask &= ~(1u << b);
+  else bq.q[b] = G[g].link;
+}
+
 // ORDER: P_BFS, P_SORTED or P_HYBRID
 template <int B, int ORDER, bool GHOST>
 __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
@@ -182,20 +303,27 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
   const uint32_t gen = next_generation(sp.hdr, vis, vb);
 
   uint32_t ng = 0, head = 0;
+  Buckets bq;
+  bq.q = reinterpret_cast<uint16_t*>(sp.hdr + 4);
+  bq.mask = 0;
+  bq.depth = 0;
   auto push = [&](uint32_t bin, uint32_t m, uint32_t parent) {
     Group g;
     g.bin = bin;
     g.meta = m;
-    g.parent = parent;
+    g.parent = (uint16_t)parent;
+    g.link = 0;
     g.next = 0;
-    uint32_t depth = (ORDER == P_HYBRID && parent != ~0u) ? (G[parent >> 3].key >> 4) + 1u : 0u;
+    uint32_t depth = (ORDER == P_HYBRID && parent != NO_PARENT) ? (G[parent >> 3].key >> 4) + 1u : 0u;
     g.key = (uint16_t)(depth * 16 + spawn_of(m));
     g.stale = 0;
-    G[ng++] = g;
+    G[ng] = g;
+    if (ORDER != P_BFS) bucket_push(bq, G, bucket_of(ORDER, g.key), ng);
+    ng++;
     vis_insert(vis, vb, gen, bin);
   };
-  push(b0, v0.m, ~0u);
-  push(b1, v1.m, ~0u);
+  push(b0, v0.m, NO_PARENT);
+  push(b1, v1.m, NO_PARENT);
 
   for (;;) {
     // one round: up to spawn_k spawns in candidate order, their bins
@@ -207,19 +335,21 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
     uint32_t nr = 0;
     bool out = false;  // budget spent during the round
     while (nr < t.spawn_k) {
-      while (head < ng && G[head].next >= B) head++;
-      if (head == ng) break;  // nothing left to spawn
-      uint32_t g = head;
-      if (ORDER != P_BFS) {
-        uint32_t best = G[head].key;
-        for (uint32_t q = head + 1; q < ng; q++) {
-          Group gq = G[q];
-          if (gq.next < B && gq.key < best) { best = gq.key; g = q; }
-        }
+      uint32_t g;
+      int bk = 0;
+      if (ORDER == P_BFS) {  // the oldest group with a record left
+        while (head < ng && G[head].next >= B) head++;
+        if (head == ng) break;  // nothing left to spawn
+        g = head;
+      } else {  // the smallest key, oldest first among equals
+        bk = bucket_min(ORDER, bq);
+        if (bk < 0) break;
+        g = bq.q[bk];
       }
       Group gr = G[g];
       uint32_t s = gr.next;
       G[g].next = (uint8_t)(s + 1);
+      if (ORDER != P_BFS && s + 1 >= B) bucket_pop(bq, G, (uint32_t)bk, g);
       if ((gr.meta >> s) & 1u) {  // claimed by another insertion: ignore it (Sec. 8)
         c.foreign = 1;
         continue;
@@ -269,7 +399,7 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
       }
       // path root -> ... -> (g, s): depth entries in chain order
       uint32_t depth = 1;
-      for (uint32_t q = g; G[q].parent != ~0u; q = G[q].parent >> 3) depth++;
+      for (uint32_t q = g; G[q].parent != NO_PARENT; q = G[q].parent >> 3) depth++;
       if ((int)depth + 4 > c.pcap) return ST_LONG;
       {
         // entries in chain order; the group index rides in the content word
@@ -278,7 +408,7 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
         for (int e = (int)depth - 1; e >= 0; e--) {
           set_entry(c, e, pack_entry(G[q].bin, (int)qs, K_MOVE, false, 0, 0), q);
           uint32_t par = G[q].parent;
-          if (par != ~0u) { qs = par & 7u; q = par >> 3; }
+          if (par != NO_PARENT) { qs = par & 7u; q = par >> 3; }
         }
       }
       // claim the path in chain order; each CAS checks its bin is as viewed,
@@ -337,64 +467,85 @@ __device__ int insert_search_dary(const DevTable& t, Ctx& c, uint8_t* region) {
   const uint32_t gen = next_generation(sp.hdr, vis, vb);
 
   uint32_t ng = 0, head = 0;
+  Buckets bq;
+  bq.q = reinterpret_cast<uint16_t*>(sp.hdr + 4);
+  bq.mask = 0;
+  bq.depth = 0;
   auto push = [&](uint32_t bin, uint32_t m, uint32_t parent) {
     Group g;
     g.bin = bin;
     g.meta = m;
-    g.parent = parent;
+    g.parent = (uint16_t)parent;
+    g.link = 0;
     g.next = 0;
-    uint32_t depth = (ORDER == P_HYBRID && parent != ~0u) ? (G[parent >> 3].key >> 4) + 1u : 0u;
+    uint32_t depth = (ORDER == P_HYBRID && parent != NO_PARENT) ? (G[parent >> 3].key >> 4) + 1u : 0u;
     g.key = (uint16_t)(depth * 16 + spawn_of(m));
     g.stale = 0;
-    G[ng++] = g;
+    G[ng] = g;
+    if (ORDER != P_BFS) bucket_push(bq, G, bucket_of(ORDER, g.key), ng);
+    ng++;
     vis_insert(vis, vb, gen, bin);
   };
-  for (uint32_t i = 0; i < d; i++) push(b[i], v[i].m, ~0u);
+  for (uint32_t i = 0; i < d; i++) push(b[i], v[i].m, NO_PARENT);
 
+  GroupCache<4> k;  // BFS: the head group's record, its bins and which of them may be tried
+  k.g = ~0u;
   for (;;) {
     // rounds of spawn_k tries, as in the two-choice searches
     uint32_t rg[8], ry[8];
     uint32_t nr = 0;
     bool out = false;
     while (nr < t.spawn_k) {
-      while (head < ng && G[head].next >= d) head++;
-      if (head == ng) break;  // nothing left to try
-      uint32_t g = head;
-      if (ORDER != P_BFS) {
-        uint32_t best = G[head].key;
-        for (uint32_t q = head + 1; q < ng; q++) {
-          Group gq = G[q];
-          if (gq.next < d && gq.key < best) { best = gq.key; g = q; }
+      uint32_t g, j, y;
+      if (ORDER == P_BFS) {  // the oldest group, until its hash functions run out
+        if (k.g == head && k.next >= d) head++;
+        if (head == ng) break;  // nothing left to try
+        if (k.g != head) take_group_dary(t, G, head, vis, vb, gen, k);
+        g = head;
+        j = k.next++;
+        if (k.meta & 1u) {  // claimed by another insertion: ignore it (Sec. 8)
+          c.foreign = 1;
+          continue;
         }
-      }
-      Group gr = G[g];
-      uint32_t j = gr.next;
-      G[g].next = (uint8_t)(j + 1);
-      if (gr.meta & 1u) {  // claimed by another insertion: ignore it (Sec. 8)
-        c.foreign = 1;
-        continue;
-      }
-      uint64_t rec = ld_slot(t.slots + gr.bin);
-      if (rec == EMPTY) continue;
-      uint32_t rb[4];
-      bins_of(t, key_of(rec), rb);
-      uint32_t y = rb[j];
-      if (y == gr.bin || vis_has(vis, vb, gen, y)) continue;
-      if (ORDER != P_BFS && spawn_of(gr.meta) < 15) {
-        uint32_t nm = gr.meta + (1u << SPAWN_SHIFT);
-        if (cas_acquire(t.meta + gr.bin, gr.meta, nm)) {
-          G[g].meta = nm;
-        } else {
-          G[g].stale = 1;
-          uint32_t m = ld_acquire(t.meta + gr.bin);
-          for (int k = 0; k < 64 && spawn_of(m) < 15; k++) {  // bounded: a lost count is harmless
-            if (cas_acquire(t.meta + gr.bin, m, m + (1u << SPAWN_SHIFT))) break;
-            m = ld_acquire(t.meta + gr.bin);
+        // empty, the record's own bin, or a bin already viewed
+        if (!((k.ok >> j) & 1u)) continue;
+        y = pick<4>(k.y, j);
+        if (spawned_to<4>(k, y)) continue;
+      } else {  // the smallest key, oldest first among equals
+        const int bk = bucket_min(ORDER, bq);
+        if (bk < 0) break;
+        g = bq.q[bk];
+        Group gr = G[g];
+        j = gr.next;
+        G[g].next = (uint8_t)(j + 1);
+        if (j + 1 >= d) bucket_pop(bq, G, (uint32_t)bk, g);
+        if (gr.meta & 1u) {
+          c.foreign = 1;
+          continue;
+        }
+        uint64_t rec = ld_slot(t.slots + gr.bin);
+        if (rec == EMPTY) continue;
+        uint32_t rb[4];
+        bins_of(t, key_of(rec), rb);
+        y = rb[j];
+        if (y == gr.bin || vis_has(vis, vb, gen, y)) continue;
+        if (spawn_of(gr.meta) < 15) {
+          uint32_t nm = gr.meta + (1u << SPAWN_SHIFT);
+          if (cas_acquire(t.meta + gr.bin, gr.meta, nm)) {
+            G[g].meta = nm;
+          } else {
+            G[g].stale = 1;
+            uint32_t m = ld_acquire(t.meta + gr.bin);
+            for (int q = 0; q < 64 && spawn_of(m) < 15; q++) {  // bounded: a lost count is harmless
+              if (cas_acquire(t.meta + gr.bin, m, m + (1u << SPAWN_SHIFT))) break;
+              m = ld_acquire(t.meta + gr.bin);
+            }
           }
         }
       }
       if (c.viewed - c.viewed0 >= sp.budget || ng + nr >= sp.max_groups) { out = true; break; }  // budget spent
       vis_insert(vis, vb, gen, y);
+      if (ORDER == P_BFS) k.spawned |= 1u << j;
       c.viewed++;
       prefetch_bin<1>(t, y);
       rg[nr] = g;
@@ -413,13 +564,13 @@ __device__ int insert_search_dary(const DevTable& t, Ctx& c, uint8_t* region) {
       }
       // path: root group -> ... -> group g, one record each, in chain order
       uint32_t depth = 1;
-      for (uint32_t q = g; G[q].parent != ~0u; q = G[q].parent >> 3) depth++;
+      for (uint32_t q = g; G[q].parent != NO_PARENT; q = G[q].parent >> 3) depth++;
       if ((int)depth + 4 > c.pcap) return ST_LONG;
       {
         uint32_t q = g;
         for (int e = (int)depth - 1; e >= 0; e--) {
           set_entry(c, e, pack_entry(G[q].bin, 0, K_MOVE, false, 0, 0), q);
-          if (G[q].parent != ~0u) q = G[q].parent >> 3;
+          if (G[q].parent != NO_PARENT) q = G[q].parent >> 3;
         }
       }
       // claim the path in chain order from the metadata words as viewed; the
