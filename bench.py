@@ -332,13 +332,16 @@ def policy_fills(torch, ck, stream, base_keys, only=None):
                       ("sorted+ghost", ck.SORTED | ck.GHOST), ("queue+ghost", ck.QUEUE | ck.GHOST),
                       ("hybrid", ck.HYBRID), ("hybrid+ghost", ck.HYBRID | ck.GHOST),
                       ("bfs_k4", ck.BFS | 0x10000), ("sorted_k4", ck.SORTED | 0x10000),
-                      ("sorted+ghost_k4", ck.SORTED | ck.GHOST | 0x10000)):
-        # 0x10000 here: searches spawning 4 records a round (Sec. 5 prefetching)
+                      ("sorted+ghost_k4", ck.SORTED | ck.GHOST | 0x10000), ("bfs_warp", ck.BFS | 0x20000)):
+        # 0x10000 here: searches spawning 4 records a round (Sec. 5 prefetching);
+        # 0x20000: breadth-first search by a warp per key (CK_PARAM_SEARCH_WARP)
         if only and name not in only:
             continue
         t = ck.CuckooTable(BINS, B, 2, pol & 0xFFFF, seed=1)
         if pol & 0x10000:
             t.set_param(ck.PARAM_SPAWN_K, 4)
+        if pol & 0x20000:
+            t.set_param(ck.PARAM_SEARCH_WARP, 1)
         fill_once(torch, ck, t, kt, vt, st, stream)  # warm
         ms, _ = fill_once(torch, ck, t, kt, vt, st, stream)
         s = t.stats()

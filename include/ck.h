@@ -90,6 +90,16 @@ extern "C" {
                                     share of a table's slots in flight, so a small table can
                                     fill faster with fewer insertions at once, each thread
                                     taking more keys. */
+#define CK_PARAM_SEARCH_WARP 36 /* 1: breadth-first search on a two-choice table without ghosts
+                                   is run by a whole warp per key (spawn_k 1 only): the
+                                   candidates of the search order are viewed 32 at a time and
+                                   the first with room in that order ends the search, so it
+                                   views more bins (all counted) in fewer round trips; the
+                                   search state stays in shared memory.  Searches longer than
+                                   256 groups or out of budget continue as CK_BFS does.
+                                   Concurrent inserts only (CK_INS_SERIAL and CK_INS_UPSERT
+                                   run the per-thread kernel).  Default 0; CK_EINVAL for any
+                                   other table. */
 #define CK_PARAM_HASH_FAMILY 33 /* 0 (default): h_i = fmix32(k ^ seed_i); 1: decorrelated
                                    h_i = fmix32(fmix32(k + seed_i) ^ (seed_i * 0x27D4EB2F)).
                                    Set before the first insertion. */

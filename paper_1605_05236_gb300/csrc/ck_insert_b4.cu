@@ -6,5 +6,6 @@
 namespace ck {
 
 InsertFn pick_insert_b4(uint32_t policy, bool ghost) { return pick_two_choice<4>(policy, ghost); }
+InsertFn pick_insert_warp_b4() { return launch_insert_warp<4>; }
 
 }  // namespace ck

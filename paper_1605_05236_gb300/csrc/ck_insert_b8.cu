@@ -6,5 +6,6 @@
 namespace ck {
 
 InsertFn pick_insert_b8(uint32_t policy, bool ghost) { return pick_two_choice<8>(policy, ghost); }
+InsertFn pick_insert_warp_b8() { return launch_insert_warp<8>; }
 
 }  // namespace ck

@@ -6,6 +6,7 @@
 
 #include "ck.h"
 #include "ck_kernels.cuh"
+#include "ck_warp.cuh"
 
 namespace ck {
 
@@ -26,6 +27,8 @@ using InsertFn = cudaError_t (*)(const InsertLaunch& l, const uint32_t* keys, co
 InsertFn pick_insert_b1(uint32_t policy);
 InsertFn pick_insert_b4(uint32_t policy, bool ghost);
 InsertFn pick_insert_b8(uint32_t policy, bool ghost);
+InsertFn pick_insert_warp_b4();  // BFS by a warp per search (CK_PARAM_SEARCH_WARP)
+InsertFn pick_insert_warp_b8();
 
 template <int B, int POL, bool GHOST>
 cudaError_t launch_insert(const InsertLaunch& l, const uint32_t* keys, const uint32_t* vals, uint64_t n,
@@ -69,6 +72,39 @@ cudaError_t launch_insert(const InsertLaunch& l, const uint32_t* keys, const uin
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_insert<B, POL, GHOST, false>, dt, keys, vals, n, st, viewed, load_base, upsert);
+}
+
+// The warp-search form of BFS (two-choice, no ghosts, concurrent only).
+template <int B>
+cudaError_t launch_insert_warp(const InsertLaunch& l, const uint32_t* keys, const uint32_t* vals, uint64_t n,
+                               uint8_t* st, uint32_t* viewed, bool, uint32_t, cudaStream_t s) {
+  const DevTable& dt = *l.dt;
+  static int cached_per_sm = 0;
+  if (cached_per_sm == 0) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_insert_warp<B>, WARP_BLOCK, 0) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    cached_per_sm = per_sm;
+  }
+  uint64_t grid = (n + WARP_BLOCK - 1) / WARP_BLOCK;
+  const uint64_t resident = (uint64_t)cached_per_sm * l.sm_count;
+  if (grid > resident) grid = resident;
+  const uint64_t by_threads = l.max_threads / WARP_BLOCK;
+  if (grid > by_threads) grid = by_threads > 0 ? by_threads : 1;
+  const uint64_t cap_blocks = (dt.n_searchers / SLAB) / ((WARP_BLOCK + SLAB - 1) / SLAB);
+  if (grid > cap_blocks) grid = cap_blocks;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(WARP_BLOCK);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = l.overlap ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_insert_warp<B>, dt, keys, vals, n, st, viewed, l.load_base);
 }
 
 // The two-choice policies for one bin size.
