@@ -27,6 +27,7 @@ ROWS = {
     "rattle_d3_0.90": (1 << 26, 1, 3, oracle.RATTLE, 0.90, 500, 0, 2, 1),
     "rattle_d3_0.90_hash1": (1 << 26, 1, 3, oracle.RATTLE, 0.90, 500, 1, 2, 1),
     "rattle_d4_0.96": (1 << 26, 1, 4, oracle.RATTLE, 0.96, 500, 0, 2, 1),
+    "rattle_d4_0.96_hash1": (1 << 26, 1, 4, oracle.RATTLE, 0.96, 500, 1, 2, 1),
     "hybrid_d4_0.96": (1 << 26, 1, 4, oracle.HYBRID, 0.96, 500, 0, 2, 1),
     "hybrid_d4_0.96_hash1": (1 << 26, 1, 4, oracle.HYBRID, 0.96, 500, 1, 2, 1),
 }

@@ -119,22 +119,26 @@ def test_l2_resident_small_table_matches_the_oracle():
     assert np.array_equal(ck.u32_numpy(v), ov)
 
 
-# (choices, load, policy, hash family, chain cap): the single-slot workloads
-# at their full size, in the bench's launch configuration (2^20-key calls on
-# one stream, launches overlapping)
-DARY_FULL = [(3, 0.90, ck.RANDOM, 0, 4096), (4, 0.96, ck.RATTLE, 1, 500)]
+# (choices, load, policy, hash family, chain cap, name of the serial oracle's
+# failure count in tests/golden/full_size_failures.json): the single-slot
+# workloads at their full size, in the bench's launch configuration (2^20-key
+# calls on one stream, launches overlapping)
+DARY_FULL = [(3, 0.90, ck.RANDOM, 0, 4096, None), (4, 0.96, ck.RATTLE, 1, 500, "rattle_d4_0.96_hash1")]
 
 
 @pytest.mark.timeout(900)
-@pytest.mark.parametrize("d,load,policy,family,cap", DARY_FULL,
+@pytest.mark.parametrize("d,load,policy,family,cap,oname", DARY_FULL,
                          ids=["d%d-%.2f-%x-hash%d" % (c[0], c[1], c[2], c[3]) for c in DARY_FULL])
-def test_dary_full_size_fill_and_lookups(d, load, policy, family, cap):
+def test_dary_full_size_fill_and_lookups(d, load, policy, family, cap, oname):
     """2^26 single-slot bins filled to 0.90 (d = 3, random kicking) or 0.96
     (d = 4, rattle-kicking) in 2^20-key calls, then 2^26 lookups at 50% hits.
     Properties that hold at any size, checked over every record: every key
-    inserted (these fills fail no key in the serial oracle either) and found
-    with its value, every absent key missed, each record in one of its d
-    bins, no key stored twice, no claim left set, the size counter exact."""
+    inserted except at most as many as the serial oracle fails at the same
+    cap (none for the random walks; 3 of 64.4 M for rattle-kicking, whose
+    walks reach the cap of 500 tries), each key reported FAILED absent, every
+    other key found with its value, every absent key missed, each record in
+    one of its d bins, no key stored twice, no claim left set, the size
+    counter exact."""
     bins = 1 << 26
     n = inputs.load_target(bins, load)
     keys, nxt = inputs.distinct_keys(n, 2)
@@ -148,9 +152,17 @@ def test_dary_full_size_fill_and_lookups(d, load, policy, family, cap):
     for lo in range(0, n, bench.BATCH):
         t.insert_batch(kt[lo:lo + bench.BATCH], vt[lo:lo + bench.BATCH], st[lo:lo + bench.BATCH], s)
     torch.cuda.synchronize()
-    assert bool((st == 0).all().item()), np.bincount(st.cpu().numpy())
-    assert t.stats()["size"] == n
+    sn = st.cpu().numpy()
+    allowed = bench.oracle_full_size_failures()[oname]["failed"] if oname else 0
+    failed = sn == 1
+    assert ((sn == 0) | failed).all(), np.bincount(sn)
+    assert failed.sum() <= allowed, (failed.sum(), allowed)
+    assert t.stats()["size"] == n - failed.sum()
     lk, expect = inputs.lookup_keys(keys, 1 << 26, 2, 0.5, next_start=nxt)
+    if failed.any():  # a key left out is absent
+        expect = expect & ~np.isin(lk, keys[failed]).astype(np.uint8)
+        _, ff = t.lookup(ck.as_u32_tensor(keys[failed]))
+        assert not ff.cpu().numpy().any()
     v, f = t.lookup(ck.as_u32_tensor(lk))
     f = f.cpu().numpy()
     assert np.array_equal(f, expect)
@@ -158,7 +170,7 @@ def test_dary_full_size_fill_and_lookups(d, load, policy, family, cap):
     assert np.array_equal(ck.u32_numpy(v)[hit], inputs.values_for(lk[hit]))
     slots, meta = t.export()
     info = check_table(slots, meta, bins, 1, d, family)
-    assert info["size"] == n
+    assert info["size"] == n - failed.sum()
     t.close()
 
 
