@@ -96,10 +96,14 @@ extern "C" {
                                    the first with room in that order ends the search, so it
                                    views more bins (all counted) in fewer round trips; the
                                    search state stays in shared memory.  Searches longer than
-                                   256 groups or out of budget continue as CK_BFS does.
+                                   128 groups or out of budget continue as CK_BFS does.
                                    Concurrent inserts only (CK_INS_SERIAL and CK_INS_UPSERT
                                    run the per-thread kernel).  Default 0; CK_EINVAL for any
                                    other table. */
+#define CK_PARAM_SEARCH_WARP_LOAD 37 /* with CK_PARAM_SEARCH_WARP: the warp form runs only the
+                                        insert calls that start with the table at least this
+                                        full, in thousandths (0..1000; default 0: every call);
+                                        the calls before run the per-thread kernel. */
 #define CK_PARAM_HASH_FAMILY 33 /* 0 (default): h_i = fmix32(k ^ seed_i); 1: decorrelated
                                    h_i = fmix32(fmix32(k + seed_i) ^ (seed_i * 0x27D4EB2F)).
                                    Set before the first insertion. */

@@ -27,7 +27,7 @@ GHOST = 0x100
 PARAM_CHAIN_CAP, PARAM_MAX_RETRIES, PARAM_RNG_SEED = 1, 2, 3
 PARAM_HASH_SEED0, PARAM_BLOCK = 10, 20
 PARAM_RATTLE_TIE_RESIDENT, PARAM_ORDERED_WRITES, PARAM_OVERLAP, PARAM_HASH_FAMILY = 30, 31, 32, 33
-PARAM_SPAWN_K, PARAM_MAX_INFLIGHT, PARAM_SEARCH_WARP = 34, 35, 36
+PARAM_SPAWN_K, PARAM_MAX_INFLIGHT, PARAM_SEARCH_WARP, PARAM_SEARCH_WARP_LOAD = 34, 35, 36, 37
 INS_SERIAL, INS_UPSERT = 1, 2
 HIST_BUCKETS = 200
 

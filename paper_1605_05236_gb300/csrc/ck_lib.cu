@@ -25,7 +25,8 @@ struct ck_table {
   uint32_t block;
   uint32_t policy_code;  // as passed by the caller (policy | ghost flag)
   uint64_t max_inflight; // insertions in flight per insert launch at most (0: as many as fit)
-  uint32_t search_warp;  // BFS searches run by a whole warp (ck_warp.cuh)
+  uint32_t search_warp;  // BFS searches run by a whole warp (ck_warp.cuh) ...
+  uint32_t search_warp_load;  // ... in launches that start at a load of at least this / 1000
 };
 
 namespace {
@@ -162,6 +163,7 @@ int init_table(ck_table* t, void* buf, size_t bytes, bool owns, uint64_t bins, u
   t->policy_code = policy;
   t->max_inflight = 0;
   t->search_warp = 0;
+  t->search_warp_load = 0;
   if (cudaGetDevice(&t->device) != cudaSuccess) return CK_ECUDA;
   if (cudaDeviceGetAttribute(&t->sm_count, cudaDevAttrMultiProcessorCount, t->device) != cudaSuccess)
     return CK_ECUDA;
@@ -322,6 +324,10 @@ int ck_set_param(ck_table* t, int key, int64_t value) {
       if (value && (d.B == 1 || d.ghost || d.policy != CK_BFS)) return CK_EINVAL;
       t->search_warp = (uint32_t)value;
       return CK_OK;
+    case CK_PARAM_SEARCH_WARP_LOAD:
+      if (value < 0 || value > 1000) return CK_EINVAL;
+      t->search_warp_load = (uint32_t)value;
+      return CK_OK;
     case CK_PARAM_HASH_FAMILY:
       if (value != 0 && value != 1) return CK_EINVAL;
       d.hash_family = (uint32_t)value;
@@ -343,7 +349,8 @@ int ck_insert_batch_ex(ck_table* t, const uint32_t* d_keys, const uint32_t* d_va
   if (!d_keys || !d_vals) return CK_EINVAL;
   if (flags & ~(uint32_t)(CK_INS_SERIAL | CK_INS_UPSERT)) return CK_EINVAL;
   InsertFn fn = pick_insert(t);
-  if (t->search_warp && t->dt.spawn_k == 1 && !(flags & (CK_INS_SERIAL | CK_INS_UPSERT)))
+  if (t->search_warp && t->dt.spawn_k == 1 && !(flags & (CK_INS_SERIAL | CK_INS_UPSERT)) &&
+      t->load_base * 1000 >= (uint64_t)t->search_warp_load * t->dt.total_slots)
     fn = t->dt.B == 4 ? pick_insert_warp_b4() : pick_insert_warp_b8();
   if (!fn) return CK_ENOTSUP;
   const InsertLaunch l{&t->dt, t->block, t->sm_count, t->overlap != 0, t->load_base,

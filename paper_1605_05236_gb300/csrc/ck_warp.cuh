@@ -21,8 +21,8 @@
 // search (counted as viewed), and in exchange takes one round trip for up
 // to 32 of them.  The owner lane claims the path and its terminal exactly
 // as the per-thread search does (ck_search.cuh) and commits with the same
-// code.  A search that needs more groups than shared memory holds (256;
-// 128 for 8-slot bins), or runs out of budget, is handed to the per-thread
+// code.  A search that needs more groups than shared memory holds (128),
+// or runs out of budget, is handed to the per-thread
 // search (which retries in a larger space), so every key ends as it would
 // in k_insert.
 #pragma once
@@ -30,10 +30,11 @@
 
 namespace ck {
 
-// groups one warp search keeps in shared memory (8-slot bins: fewer, so
-// that a block's four warps stay within 48 KB)
+// groups one warp search keeps in shared memory: 128 keeps the 4-slot
+// kernel at 8 blocks (32 warps) per SM; 256 (6 blocks) made the 2^24 x 4
+// BFS fill with the warp form 14% slower
 template <int B>
-__host__ __device__ constexpr int warp_groups() { return B == 4 ? 256 : 128; }
+__host__ __device__ constexpr int warp_groups() { return 128; }
 constexpr unsigned FULL_MASK = 0xFFFFFFFFu;
 constexpr int WARP_BLOCK = 128;        // threads per block of k_insert_warp
 

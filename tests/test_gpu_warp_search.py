@@ -1,10 +1,11 @@
 """Breadth-first search by a whole warp (CK_PARAM_SEARCH_WARP) against the
 serial oracle's BFS: the same key -> value map after concurrent fills to
 high loads (4- and 8-slot bins, tables from a few thousand bins to 2^20,
-batches that span many warps and leave a ragged tail), every table
-invariant, every lookup as the oracle answers it; the searches view at
-least the bins the serial search views (a round views 32 candidates at
-once); and the parameter is refused for every table it does not apply to."""
+batches that span many warps and leave a ragged tail; the warp form in
+every call, or only from a given load on), every table invariant, every
+lookup as the oracle answers it; the searches view at least the bins the
+serial search views (a round views 32 candidates at once); and the
+parameters are refused for every table and value they do not apply to."""
 import numpy as np
 import pytest
 import torch
@@ -15,14 +16,18 @@ from table_checks import check_table
 
 pytestmark = pytest.mark.gpu
 
-# (bins, slots per bin, load, batch): small tables with many keys in flight,
-# and a 2^20 x 4 table filled to 0.95 in 2^16-key batches
-CASES = [(1 << 12, 4, 0.95, 1000), (1 << 14, 4, 0.95, 4099), (1 << 13, 8, 0.97, 3001),
-         (1 << 20, 4, 0.95, 1 << 16), (1 << 17, 8, 0.98, 1 << 14)]
+# (bins, slots per bin, load, batch, load in thousandths from which the
+# warp form runs): small tables with many keys in flight, a 2^20 x 4 table
+# filled to 0.95 in 2^16-key batches, and fills whose early batches run the
+# per-thread kernel and later ones the warp form
+CASES = [(1 << 12, 4, 0.95, 1000, 0), (1 << 14, 4, 0.95, 4099, 0), (1 << 13, 8, 0.97, 3001, 0),
+         (1 << 20, 4, 0.95, 1 << 16, 0), (1 << 17, 8, 0.98, 1 << 14, 0), (1 << 20, 4, 0.95, 1 << 16, 850),
+         (1 << 14, 8, 0.97, 2048, 500)]
 
 
-@pytest.mark.parametrize("bins,b,load,batch", CASES, ids=["%dx%d-%.2f" % c[:3] for c in CASES])
-def test_warp_bfs_matches_oracle(bins, b, load, batch):
+@pytest.mark.parametrize("bins,b,load,batch,from_load", CASES, ids=["%dx%d-%.2f-from%d" % (c[0], c[1], c[2], c[4])
+                                                                   for c in CASES])
+def test_warp_bfs_matches_oracle(bins, b, load, batch, from_load):
     n = inputs.load_target(bins * b, load)
     keys, nxt = inputs.distinct_keys(n, 5)
     vals = inputs.values_for(keys)
@@ -30,6 +35,7 @@ def test_warp_bfs_matches_oracle(bins, b, load, batch):
     assert (ref.insert(keys, vals) == 0).all()
     t = ck.CuckooTable(bins, b, 2, ck.BFS, seed=3)
     t.set_param(ck.PARAM_SEARCH_WARP, 1)
+    t.set_param(ck.PARAM_SEARCH_WARP_LOAD, from_load)
     kt, vt = ck.as_u32_tensor(keys), ck.as_u32_tensor(vals)
     st = torch.full((n,), 255, dtype=torch.uint8, device="cuda")
     for lo in range(0, n, batch):
@@ -80,4 +86,7 @@ def test_search_warp_refused_elsewhere(bins, b, d, policy):
     with pytest.raises(RuntimeError):
         t.set_param(ck.PARAM_SEARCH_WARP, 1)
     t.set_param(ck.PARAM_SEARCH_WARP, 0)
+    for bad in (-1, 1001):
+        with pytest.raises(RuntimeError):
+            t.set_param(ck.PARAM_SEARCH_WARP_LOAD, bad)
     t.close()
