@@ -13,8 +13,14 @@ from table_checks import check_table
 
 pytestmark = pytest.mark.gpu
 
-CASES = [(1 << 12, 4, 2, ck.QUEUE), (1 << 12, 4, 2, ck.SORTED | ck.GHOST), (1 << 11, 8, 2, ck.RANDOM | ck.GHOST),
-         (1 << 14, 1, 3, ck.RATTLE), (1 << 14, 1, 4, ck.HYBRID)]
+# (bins, slots per bin, choices, policy, hash family).  Rattle-kicking with
+# three choices ends at load 0.90, close to where its walks start to reach
+# the cap of 500 under the XOR hash family (the full-size serial fill to
+# 0.90 fails 0.7% of its keys), and concurrent batches, whose order differs
+# from the serial one, then fail a key now and then: it runs under the
+# decorrelated family (1 failure in 60.4 M at full size).
+CASES = [(1 << 12, 4, 2, ck.QUEUE, 0), (1 << 12, 4, 2, ck.SORTED | ck.GHOST, 0),
+         (1 << 11, 8, 2, ck.RANDOM | ck.GHOST, 0), (1 << 14, 1, 3, ck.RATTLE, 1), (1 << 14, 1, 4, ck.HYBRID, 0)]
 
 
 def workload(bins, B, seed):
@@ -27,12 +33,14 @@ def workload(bins, B, seed):
     return pre, ks, vs
 
 
-@pytest.mark.parametrize("bins,B,d,policy", CASES, ids=lambda x: str(x))
+@pytest.mark.parametrize("bins,B,d,policy,family", CASES, ids=lambda x: str(x))
 @pytest.mark.parametrize("serial", [True, False])
-def test_upsert_matches_oracle(bins, B, d, policy, serial):
+def test_upsert_matches_oracle(bins, B, d, policy, family, serial):
     pre, ks, vs = workload(bins, B, 21)
     ref = oracle.OracleTable(bins, B, d, policy, rng_seed=5, cap=500)
+    ref.set_hash_family(family)
     t = ck.CuckooTable(bins, B, d, policy, seed=5)
+    t.set_param(ck.PARAM_HASH_FAMILY, family)
     assert (ref.insert(pre, inputs.values_for(pre)) == 0).all()
     t.insert(ck.as_u32_tensor(pre), ck.as_u32_tensor(inputs.values_for(pre)), serial=True)
     torch.cuda.synchronize()
@@ -48,6 +56,6 @@ def test_upsert_matches_oracle(bins, B, d, policy, serial):
     slots, meta = t.export()
     if serial:
         assert np.array_equal(slots, ref.export()["rec"])
-    check_table(slots, meta, bins, B, d)
+    check_table(slots, meta, bins, B, d, family)
     v, f = t.lookup(ck.as_u32_tensor(ks))
     assert bool((f == 1).all()) and np.array_equal(ck.u32_numpy(v), vs)
