@@ -545,7 +545,7 @@ def multi_form(torch, ck, stream):
 # its 61 launches) from an ncu capture of the current kernel build: a
 # half-size fill (2^23 x 4, the same 61-launch load trajectory, half the keys
 # per launch), scaled by 2; None until captured for this build
-INSERT_TRAFFIC_PER_LAUNCH = 386_800_000
+INSERT_TRAFFIC_PER_LAUNCH = 387_000_000
 
 SERVE_BINS = 1 << 26
 SERVE_PREFILL = 255013683  # floor(0.95 * 2^28)
