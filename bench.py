@@ -362,6 +362,7 @@ def policy_fills(torch, ck, stream, base_keys, only=None):
     del kt, vt, st
     # 8-slot bins at 0.99 and the d-ary tables of the same slot count
     lookup_cache = {}
+    gathers = {}  # width -> (GB/s, shape) of the measured random gather
     for name, bins, b, d, pol, load, cap in (
             ("queue_b8_0.99", 1 << 23, 8, 2, ck.QUEUE, 0.99, 500),
             ("random_b8_0.99", 1 << 23, 8, 2, ck.RANDOM, 0.99, 500),
@@ -397,7 +398,7 @@ def policy_fills(torch, ck, stream, base_keys, only=None):
                                                        if q <= load)),
                "chain_max": s["chain_max"], "chain": chain_summary(t.chain_histogram()),
                "failed": s["inserts_failed"], "aborted": s["inserts_aborted"]}
-        if d > 2:
+        if d > 2 or b == 8:
             ck_key = (bins, d, load)
             if ck_key not in lookup_cache:
                 lookup_cache.clear()
@@ -415,6 +416,16 @@ def policy_fills(torch, ck, stream, base_keys, only=None):
             rec["m_lookups_per_s"] = round(N_LOOKUP / e0.elapsed_time(e1) / 1e3, 1)
             rec["lookups_exact"] = bool(torch.equal(f.cpu(), torch.from_numpy(expect)))
             del lkt, v, f
+            # against the measured random gather of the lookup's own width: d
+            # single-slot bins of 8 B, or two 8-slot bins of 64 B, per lookup
+            width, per_lookup = (8, 8 * d) if d > 2 else (64, 128)
+            if width not in gathers:
+                gathers[width] = gather_roofline(torch, ck, bins * b * 8, width, 1 << 26, stream)[:2]
+            g, shape = gathers[width]
+            rb = rec["m_lookups_per_s"] * 1e6 * per_lookup / 1e9
+            rec["roofline_lookup"] = {"random_bytes_gbs": round(rb, 1), "bytes_per_lookup": per_lookup,
+                                      "vs_random_gather": {"width_bytes": width, "gbs": round(g, 1),
+                                                           "shape": shape, "frac": round(rb / g, 4)}}
         if name in ofail:
             rec["oracle_failed_same_cap"] = ofail[name]["failed"]
         out[name] = rec
@@ -997,7 +1008,12 @@ def run_gpu(args, rank, world, local):
             # at the same cap (none expected)
             "failed_beyond_oracle": sorted(k for k, p in pol.items()
                                            if p.get("failed", 0) > p.get("oracle_failed_same_cap", 0)),
-            "contents_exact": all(p.get("contents_exact", True) for p in pol.values())}
+            "contents_exact": all(p.get("contents_exact", True) for p in pol.values()),
+            # lookups of the 8-slot and single-slot tables against the random
+            # gather of their own width (64 B, 8 B)
+            "lookup_vs_gather": {k: pol[r]["roofline_lookup"]["vs_random_gather"]["frac"]
+                                 for k, r in (("b8", "queue_b8_0.99"), ("d3", "random_d3_0.90"),
+                                              ("d4", "random_d4_0.96")) if "roofline_lookup" in pol.get(r, {})}}
     if rank == 0 and world == 1 and not args.no_small:
         sm = small_table(torch, ck, stream)
         sections["small_table"] = sm

@@ -66,7 +66,8 @@ def test_gpu_arm_bench_line_is_compact_and_last():
                             "host": {"nproc": 16, "machine": "aarch64", "cpu": "c" * 80}},
            "sections": {"policies": big, "transactional": big},
            "section_summary": {"policies": {"queue_vs_random_viewed_at_0.95": [7.5, 18.4], "failed_total": 0,
-                                            "contents_exact": True},
+                                            "failed_beyond_oracle": [], "contents_exact": True,
+                                            "lookup_vs_gather": {"b8": 1.0123, "d3": 0.9876, "d4": 0.9765}},
                                "batched_form": {"speedup_vs_per_table": 1.77, "m_inserts_per_s": 900.0,
                                                 "all_inserted": True},
                                "serving_form": {"mix_75_20_5": {"results_exact": True, "speedup": 16.7},
