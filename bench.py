@@ -196,7 +196,10 @@ def gather_roofline(torch, ck, nbytes, width, n_reads, stream):
         for block in (128, 256, 512):
             for per_sm in (0, 8, 16, 64):
                 max_blocks = per_sm * sms
-                ck.gather_probe_ex(buf, width, n_reads, 17, per_thread, block, max_blocks, sink, stream)  # warm
+                try:  # warm (a block too large for the kernel of this width is refused)
+                    ck.gather_probe_ex(buf, width, n_reads, 17, per_thread, block, max_blocks, sink, stream)
+                except RuntimeError:
+                    continue
                 best = None
                 for _ in range(3):
                     seed += 1

@@ -555,7 +555,9 @@ int ck_gather_probe(const void *d_buf, size_t bytes, uint32_t width, uint64_t n_
  * threads per block (a multiple of 32, at most 1024), at most `max_blocks`
  * blocks striding over the reads (0: as many blocks as it takes for one
  * pass).  ck_gather_probe is per_thread 8, block 256, max_blocks 152 * 64.
- * CK_EINVAL for any other value; asynchronous. */
+ * CK_EINVAL for any other value, and for a block larger than the probe
+ * kernel of that width and per_thread can run (64-byte reads, 8 in flight:
+ * at most 256 threads); asynchronous. */
 int ck_gather_probe_ex(const void *d_buf, size_t bytes, uint32_t width, uint64_t n_reads, uint64_t seed,
                        uint32_t per_thread, uint32_t block, uint32_t max_blocks, void *d_sink, void *stream);
 

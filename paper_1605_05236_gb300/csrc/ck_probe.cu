@@ -59,16 +59,32 @@ __global__ void k_gather(const uint64_t* __restrict__ buf, uint64_t n_records, u
   if (acc == 0x0123456789ABCDEFull) sink[tid & 1023] = acc;  // keeps the loads live
 }
 
+// The probe kernel for a width and reads in flight per thread.
 template <int W>
-cudaError_t launch_gather(uint32_t per_thread, unsigned grid, unsigned block, cudaStream_t s, const uint64_t* b,
-                          uint64_t n_records, uint64_t mask, uint64_t n_reads, uint64_t seed, uint64_t* k) {
+using GatherKernel = void (*)(const uint64_t*, uint64_t, uint64_t, uint64_t, uint64_t, uint64_t*);
+
+template <int W>
+GatherKernel<W> gather_kernel(uint32_t per_thread) {
   switch (per_thread) {
-    case 1: k_gather<W, 1><<<grid, block, 0, s>>>(b, n_records, mask, n_reads, seed, k); break;
-    case 2: k_gather<W, 2><<<grid, block, 0, s>>>(b, n_records, mask, n_reads, seed, k); break;
-    case 4: k_gather<W, 4><<<grid, block, 0, s>>>(b, n_records, mask, n_reads, seed, k); break;
-    default: k_gather<W, 8><<<grid, block, 0, s>>>(b, n_records, mask, n_reads, seed, k); break;
+    case 1: return k_gather<W, 1>;
+    case 2: return k_gather<W, 2>;
+    case 4: return k_gather<W, 4>;
+    default: return k_gather<W, 8>;
   }
-  return cudaGetLastError();
+}
+
+// CK_EINVAL when the block is larger than the kernel can run with (its
+// registers: 64-byte reads, 8 in flight, take 140 a thread, so 512-thread
+// blocks do not fit); else the launch's result.
+template <int W>
+int launch_gather(uint32_t per_thread, unsigned grid, unsigned block, cudaStream_t s, const uint64_t* b,
+                  uint64_t n_records, uint64_t mask, uint64_t n_reads, uint64_t seed, uint64_t* k) {
+  const GatherKernel<W> fn = gather_kernel<W>(per_thread);
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) return CK_ECUDA;
+  if ((int)block > a.maxThreadsPerBlock) return CK_EINVAL;
+  fn<<<grid, block, 0, s>>>(b, n_records, mask, n_reads, seed, k);
+  return cudaGetLastError() == cudaSuccess ? CK_OK : CK_ECUDA;
 }
 
 // KIND 0: red.add.u32 (no result), 1: atom.add.u32 (result used),
@@ -142,11 +158,9 @@ extern "C" int ck_gather_probe_ex(const void* d_buf, size_t bytes, uint32_t widt
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const uint64_t* b = static_cast<const uint64_t*>(d_buf);
   uint64_t* k = static_cast<uint64_t*>(d_sink);
-  cudaError_t e;
-  if (width == 8) e = launch_gather<8>(per_thread, (unsigned)grid, block, s, b, n_records, mask, n_reads, seed, k);
-  else if (width == 32) e = launch_gather<32>(per_thread, (unsigned)grid, block, s, b, n_records, mask, n_reads, seed, k);
-  else e = launch_gather<64>(per_thread, (unsigned)grid, block, s, b, n_records, mask, n_reads, seed, k);
-  return e == cudaSuccess ? CK_OK : CK_ECUDA;
+  if (width == 8) return launch_gather<8>(per_thread, (unsigned)grid, block, s, b, n_records, mask, n_reads, seed, k);
+  if (width == 32) return launch_gather<32>(per_thread, (unsigned)grid, block, s, b, n_records, mask, n_reads, seed, k);
+  return launch_gather<64>(per_thread, (unsigned)grid, block, s, b, n_records, mask, n_reads, seed, k);
 }
 
 extern "C" int ck_gather_probe(const void* d_buf, size_t bytes, uint32_t width, uint64_t n_reads,
