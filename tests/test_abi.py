@@ -81,3 +81,27 @@ def test_import_invalid_arguments_need_no_gpu():
 def test_debug_claims_invalid_arguments_need_no_gpu():
     L = ck.load()
     assert L.ck_debug_claims(None, 0, 1, 0) == ck.EINVAL
+
+
+def test_binding_constants_match_the_header():
+    """Every CK_* constant the Python bindings name (policy codes, statuses,
+    error codes, parameter keys, flags, operation kinds) has the header's
+    value.  Binding name -> header name, per module."""
+    from paper_1605_05236_gb300 import multi, serve, txn
+    src = open(os.path.join(ROOT, "include", "ck.h")).read()
+    header = {}
+    for name, val in re.findall(r"^#define CK_([A-Z0-9_]+)\s+\(?(-?(?:0x[0-9A-Fa-f]+|[0-9]+))u?\)?", src, flags=re.M):
+        header[name] = int(val, 0)
+    pairs = [(ck, n, n) for n in ("OK", "EINVAL", "ENOMEM", "ECUDA", "EBUSY", "ENOTSUP", "ST_OK", "ST_FAILED",
+                                  "ST_ABORTED", "ST_INVALID", "ST_UPDATED", "CHAIN_BUCKETS", "RANDOM", "BFS",
+                                  "SORTED", "QUEUE", "RATTLE", "HYBRID", "GHOST", "INS_SERIAL", "INS_UPSERT")]
+    pairs += [(ck, n, n) for n in header if n.startswith("PARAM_")]
+    pairs += [(multi, n, n) for n in ("MULTI_TILE", "MULTI_BLOCK", "MULTI_BLOCKS_PER_SM", "MULTI_CHAIN_CAP")]
+    pairs += [(multi, "CAPTURE_CLEAR", "MULTI_CAPTURE_CLEAR"), (multi, "CAPTURE_PER_TABLE", "MULTI_CAPTURE_PER_TABLE")]
+    pairs += [(serve, n, n) for n in ("OP_LOOKUP", "OP_INSERT", "OP_DELETE", "ST_BUSY")]
+    pairs += [(txn, n, n) for n in ("TX_INSERT", "TX_READ", "TX_OVERWRITE", "TX_DELETE")]
+    pairs += [(txn, n, "TXF_" + n) for n in ("LOCAL_RETRY", "QUEUE", "SYSTEM", "CLAIM")]
+    pairs += [(txn, "MAX_OPS", "TXN_MAX_OPS"), (txn, "N_COUNTERS", "TXN_COUNTERS")]
+    for mod, py, h in pairs:
+        assert getattr(mod, py) == header[h], (mod.__name__, py, h)
+    assert len(pairs) >= 45
