@@ -53,6 +53,17 @@ cudaError_t launch_insert(const InsertLaunch& l, const uint32_t* keys, const uin
   }
   uint64_t grid = (n + block - 1) / block;
   uint64_t resident = (uint64_t)cached_per_sm * l.sm_count;
+  // Two-choice walks whose launches overlap leave a tenth of the GPU to the
+  // next launch: its blocks start while this launch's longest walks finish.
+  // Measured, fill of 2^24 x 4 to 0.95: queue-kicking 10.24 ms against 10.58
+  // with every block resident, random kicking 22.8 against 24.3 (0.8: 10.29
+  // / 23.1); searches, which need every thread they can get, are slower
+  // that way (BFS 22.5 against 20.8) and keep the full grid.  A limit the
+  // caller sets (CK_PARAM_MAX_INFLIGHT) replaces this one.
+  if (B > 1 && (POL == P_QUEUE || POL == P_RANDOM) && l.overlap && l.max_threads == ~0ull) {
+    const uint64_t most = resident * 9 / 10;
+    resident = most > 0 ? most : 1;
+  }
   if (grid > resident) grid = resident;
   uint64_t by_threads = l.max_threads / block;  // insertions in flight at once
   if (grid > by_threads) grid = by_threads > 0 ? by_threads : 1;
