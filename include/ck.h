@@ -86,9 +86,10 @@ extern "C" {
                                    candidate order, ends the search. */
 #define CK_PARAM_MAX_INFLIGHT 35 /* insertions one insert launch keeps in flight at most
                                     (0, the default: as many threads as fit on the GPU --
-                                    nine tenths of that for random kicking and queue-kicking
-                                    on two-choice tables when launches overlap, so that the
-                                    next launch starts beside this one's longest walks; else
+                                    nine tenths of that for random kicking and queue-kicking,
+                                    eight tenths for rattle-kicking, when launches overlap,
+                                    so that the next launch starts beside this one's longest
+                                    walks; else
                                     whole blocks, one at least).  Claim conflicts grow with the
                                     share of a table's slots in flight, so a small table can
                                     fill faster with fewer insertions at once, each thread

@@ -53,15 +53,19 @@ cudaError_t launch_insert(const InsertLaunch& l, const uint32_t* keys, const uin
   }
   uint64_t grid = (n + block - 1) / block;
   uint64_t resident = (uint64_t)cached_per_sm * l.sm_count;
-  // Two-choice walks whose launches overlap leave a tenth of the GPU to the
-  // next launch: its blocks start while this launch's longest walks finish.
-  // Measured, fill of 2^24 x 4 to 0.95: queue-kicking 10.24 ms against 10.58
-  // with every block resident, random kicking 22.8 against 24.3 (0.8: 10.29
-  // / 23.1); searches, which need every thread they can get, are slower
-  // that way (BFS 22.5 against 20.8) and keep the full grid.  A limit the
-  // caller sets (CK_PARAM_MAX_INFLIGHT) replaces this one.
-  if (B > 1 && (POL == P_QUEUE || POL == P_RANDOM) && l.overlap && l.max_threads == ~0ull) {
-    const uint64_t most = resident * 9 / 10;
+  // Walks whose launches overlap leave part of the GPU to the next launch:
+  // its blocks start while this launch's longest walks finish.  Measured
+  // (whole fills, one GB300): two-choice queue-kicking 10.18 ms against
+  // 10.45-10.50 with every block resident (2^24 x 4 to 0.95) and 12.4
+  // against 14.1-14.3 (2^23 x 8 to 0.99), random kicking 22.8 against 24.5
+  // and 34.4 against 38.3; 3-ary random kicking 204.5 against 207.9 (2^26
+  // bins to 0.90); rattle-kicking keeps 0.8 of the blocks, 51.6 against
+  // 58.4 (4-ary to 0.96).  Searches, which need every thread they can get,
+  // are slower that way (BFS 22.5 against 20.8) and keep the full grid.  A
+  // limit the caller sets (CK_PARAM_MAX_INFLIGHT) replaces this one.
+  constexpr uint64_t tenths = (POL == P_QUEUE || POL == P_RANDOM) ? 9 : POL == P_RATTLE ? 8 : 10;
+  if (tenths < 10 && l.overlap && l.max_threads == ~0ull) {
+    const uint64_t most = resident * tenths / 10;
     resident = most > 0 ? most : 1;
   }
   if (grid > resident) grid = resident;
