@@ -72,6 +72,7 @@ struct Ctx {
   uint32_t viewed0;  // `viewed` when the current attempt started
   uint32_t reviews;  // bins viewed again because a claim lost a race (part of `viewed`)
   uint32_t foreign;  // the attempt ignored a slot another insertion had claimed
+  uint32_t capped;   // the attempt ended at its cap, budget or a dead end (out_of_cap)
   uint32_t kicks;    // kick-outs of the current attempt
   uint32_t draws;    // random draws of the current attempt
   uint32_t ghosts_made;
@@ -340,9 +341,30 @@ __device__ __forceinline__ bool commit(const DevTable& t, Ctx& c) {
   return true;
 }
 
-// A cap reached without meeting another insertion's claim is a genuine
-// failure; one reached after detours around claims is retried instead.
-__device__ __forceinline__ bool claims_none_foreign(const Ctx& c) { return !c.foreign; }
+// A walk or search ran out: its cap or budget, or a dead end.  Without
+// having met another insertion's claim that is the serial algorithm's
+// failure; after detours around claims it is a conflict, retried.  Either
+// way insert_one counts it as a failed attempt (capped), so a key that
+// keeps running out ends FAILED after the failed-attempt retries instead of
+// spending every conflict retry -- and with its waits between them.
+__device__ __forceinline__ int out_of_cap(Ctx& c) {
+  c.capped = 1;
+  return out_of_cap(c);
+}
+
+// Claim both free slots of a ghost pair (Sec. 4), the lower bin first: two
+// insertions whose keys hash to the same two bins in opposite order would
+// otherwise each claim its first bin, fail on the other's, release, and
+// meet again on every retry.
+__device__ __forceinline__ bool claim_ghost_pair(const DevTable& t, Ctx& c, uint32_t b0, uint32_t m0, int s0,
+                                                 uint32_t b1, uint32_t m1, int s1, bool hit) {
+  if (b1 < b0) {
+    if (!claim(t, c, b1, m1, s1, K_GHOST, hit, EMPTY)) return false;
+    return claim(t, c, b0, m0, s0, K_GHOST, hit, EMPTY);
+  }
+  if (!claim(t, c, b0, m0, s0, K_GHOST, hit, EMPTY)) return false;
+  return claim(t, c, b1, m1, s1, K_GHOST, hit, EMPTY);
+}
 
 __device__ __forceinline__ bool plan_has_bin(const Ctx& c, uint32_t bin) {
   for (int i = 0; i < c.pn; i++)
@@ -464,8 +486,7 @@ __device__ int insert_random2(const DevTable& t, Ctx& c) {
     c.viewed += 2;
     uint32_t f0 = free_mask<B>(v0), f1 = free_mask<B>(v1);
     if (f0 && f1) {
-      if (!claim(t, c, b0, v0.m, lowest(f0), K_GHOST, false, EMPTY)) return ST_CONFLICT;
-      if (!claim(t, c, b1, v1.m, lowest(f1), K_GHOST, false, EMPTY)) return ST_CONFLICT;
+      if (!claim_ghost_pair(t, c, b0, v0.m, lowest(f0), b1, v1.m, lowest(f1), false)) return ST_CONFLICT;
       c.ghosts_made++;
       return ST_OK;
     }
@@ -580,8 +601,7 @@ __device__ int insert_queue(const DevTable& t, Ctx& c) {
   if (GHOST && f0 > 0 && f1 > 0) {
     int s0 = lowest(fm0);
     int s1 = lowest(fm1);
-    if (!claim(t, c, b0, v0.m, s0, K_GHOST, true, EMPTY)) return ST_CONFLICT;
-    if (!claim(t, c, b1, v1.m, s1, K_GHOST, true, EMPTY)) return ST_CONFLICT;
+    if (!claim_ghost_pair(t, c, b0, v0.m, s0, b1, v1.m, s1, true)) return ST_CONFLICT;
     c.ghosts_made++;
     return ST_OK;
   }
@@ -631,8 +651,8 @@ __device__ int insert_queue(const DevTable& t, Ctx& c) {
         // one is not the serial algorithm's failure
         if (foreign) c.foreign = 1;
         int s = first_from<B>(um, h);
-        if (s < 0) return c.foreign ? ST_CONFLICT : ST_FAILED;
-        if (c.kicks == t.cap) return c.foreign ? ST_CONFLICT : ST_FAILED;
+        if (s < 0) return out_of_cap(c);
+        if (c.kicks == t.cap) return out_of_cap(c);
         if (int r0 = plan_room(t, c)) return r0;
         const bool rev = (own >> s) & 1u;
         const int jprev = rev ? last_entry_for(c, x, (uint32_t)s) : -1;
@@ -718,7 +738,7 @@ __device__ inline int insert_random_dary(const DevTable& t, Ctx& c) {
       c.reviews += nc;
       continue;
     }
-    if (nc == 0) return c.foreign ? ST_CONFLICT : ST_FAILED;
+    if (nc == 0) return out_of_cap(c);
     uint32_t k = (uint32_t)(draw(t, c.key, c.draws++, c.attempt) % nc);
     uint32_t x = cb[k];
     View<1> vx = cv[k];
@@ -779,7 +799,7 @@ __device__ inline int insert_rattle(const DevTable& t, Ctx& c) {
   const uint64_t* pend = nullptr;  // the slot the last kick claimed, re-read with the next view (reread)
   uint64_t pend_v = 0;
   for (uint32_t tries = 0;; tries++) {
-    if (tries == t.cap) return c.foreign ? ST_CONFLICT : ST_FAILED;
+    if (tries == t.cap) return out_of_cap(c);
     if (int r = plan_room(t, c)) return r;
     uint32_t vb[4];
     bins_of(t, key_of(cur), vb);

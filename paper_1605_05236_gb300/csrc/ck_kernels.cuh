@@ -84,6 +84,7 @@ __device__ __forceinline__ int insert_one(const DevTable& t, Ctx& c, uint8_t* re
     c.ghosts_made = 0;
     c.dup_evict = 0;
     c.foreign = 0;
+    c.capped = 0;
     if (c.long_id < 0) {
       c.pe = local_e;
       c.pcap = local_cap;
@@ -101,8 +102,12 @@ __device__ __forceinline__ int insert_one(const DevTable& t, Ctx& c, uint8_t* re
       if (c.long_id >= 0 || !grow_plan(t, c)) { st = c.long_id >= 0 ? ST_FAILED : ST_ABORTED; break; }
       continue;
     }
-    if (st == ST_FAILED) {
-      if (!retry_failed || ++fails > 6) break;
+    const bool ran_out = st == ST_FAILED || (st == ST_CONFLICT && c.capped);
+    if (ran_out) {
+      if (!retry_failed || ++fails > 6) {
+        st = ST_FAILED;
+        break;
+      }
       // a search out of budget tries again in a larger space (search_space)
       if (region && c.big_id < 0 && (POL == P_BFS || POL == P_SORTED || POL == P_HYBRID)) {
         c.big_id = acquire_long(t, c.key ^ 0x5bd1e995u);
@@ -118,7 +123,7 @@ __device__ __forceinline__ int insert_one(const DevTable& t, Ctx& c, uint8_t* re
     if (++attempt >= t.max_retries) { st = ST_ABORTED; break; }
     // a failed attempt waits longer before its retry: the walks and claims
     // of the insertions around it, which made it fail, finish meanwhile
-    backoff(st == ST_FAILED ? 6 + 2 * fails : attempt, c.key);
+    backoff(ran_out ? 6 + 2 * fails : attempt, c.key);
   }
   if (c.long_id >= 0) release_long(t, c.long_id);
   if (c.big_id >= 0) release_long(t, c.big_id);

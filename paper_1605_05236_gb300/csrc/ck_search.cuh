@@ -281,8 +281,7 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
   uint32_t f0 = free_mask<B>(v0), f1 = free_mask<B>(v1);
   if (GHOST) {
     if (f0 && f1) {
-      if (!claim(t, c, b0, v0.m, lowest(f0), K_GHOST, false, EMPTY)) return ST_CONFLICT;
-      if (!claim(t, c, b1, v1.m, lowest(f1), K_GHOST, false, EMPTY)) return ST_CONFLICT;
+      if (!claim_ghost_pair(t, c, b0, v0.m, lowest(f0), b1, v1.m, lowest(f1), false)) return ST_CONFLICT;
       c.ghosts_made++;
       return ST_OK;
     }
@@ -380,7 +379,7 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
       ry[nr] = y;
       nr++;
     }
-    if (nr == 0) return c.foreign ? ST_CONFLICT : ST_FAILED;
+    if (nr == 0) return out_of_cap(c);
     for (uint32_t i = 0; i < nr; i++) {
       const uint32_t g = rg[i], s = rs[i], y = ry[i];
       View<B> vy;
@@ -431,7 +430,7 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
       if (isdup) return take_dup<B>(t, c, y, vy, term, false);
       return take_free<B>(t, c, y, vy, term, false);
     }
-    if (out) return c.foreign ? ST_CONFLICT : ST_FAILED;
+    if (out) return out_of_cap(c);
   }
 }
 
@@ -552,7 +551,7 @@ __device__ int insert_search_dary(const DevTable& t, Ctx& c, uint8_t* region) {
       ry[nr] = y;
       nr++;
     }
-    if (nr == 0) return c.foreign ? ST_CONFLICT : ST_FAILED;
+    if (nr == 0) return out_of_cap(c);
     for (uint32_t i = 0; i < nr; i++) {
       const uint32_t g = rg[i], y = ry[i];
       View<1> vy;
@@ -589,7 +588,7 @@ __device__ int insert_search_dary(const DevTable& t, Ctx& c, uint8_t* region) {
       c.kicks = depth;
       return take_free<1>(t, c, y, vy, 0, false);
     }
-    if (out) return c.foreign ? ST_CONFLICT : ST_FAILED;
+    if (out) return out_of_cap(c);
   }
 }
 

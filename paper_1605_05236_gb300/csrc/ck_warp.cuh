@@ -304,6 +304,7 @@ __global__ void __launch_bounds__(WARP_BLOCK, 8) k_insert_warp(DevTable t, const
         c.ghosts_made = 0;
         c.dup_evict = 0;
         c.foreign = 0;
+        c.capped = 0;
         c.pe = store.e;
         c.pcap = MAX_CHAIN;
         c.pn = 0;
@@ -353,7 +354,9 @@ __global__ void __launch_bounds__(WARP_BLOCK, 8) k_insert_warp(DevTable t, const
       const WarpFound f = warp_bfs<B>(t, W, used);
       if ((int)lane == L) {
         c.viewed += f.views;
-        at = f.st == ST_OK ? warp_claim_path<B>(t, c, W, f) : f.st;
+        // a search that found nothing (claims seen on the way or not) or
+        // outgrew shared memory goes to the per-thread search
+        at = f.st == ST_OK ? warp_claim_path<B>(t, c, W, f) : f.st == ST_CONFLICT ? (int)ST_FAILED : f.st;
       }
       __syncwarp();
     }
