@@ -72,7 +72,7 @@ struct Ctx {
   uint32_t viewed0;  // `viewed` when the current attempt started
   uint32_t reviews;  // bins viewed again because a claim lost a race (part of `viewed`)
   uint32_t foreign;  // the attempt ignored a slot another insertion had claimed
-  uint32_t capped;   // the attempt ended at its cap, budget or a dead end (out_of_cap)
+  uint32_t capped;   // the attempt ended at its cap or budget, or at a dead end of its own (out_of_cap, dead_end)
   uint32_t kicks;    // kick-outs of the current attempt
   uint32_t draws;    // random draws of the current attempt
   uint32_t ghosts_made;
@@ -341,15 +341,25 @@ __device__ __forceinline__ bool commit(const DevTable& t, Ctx& c) {
   return true;
 }
 
-// A walk or search ran out: its cap or budget, or a dead end.  Without
-// having met another insertion's claim that is the serial algorithm's
-// failure; after detours around claims it is a conflict, retried.  Either
-// way insert_one counts it as a failed attempt (capped), so a key that
-// keeps running out ends FAILED after the failed-attempt retries instead of
-// spending every conflict retry -- and with its waits between them.
+// A walk or search reached its cap or budget.  Without having met another
+// insertion's claim that is the serial algorithm's failure; after detours
+// around claims it is a conflict, retried.  Either way insert_one counts it
+// as a failed attempt (capped), so a key that keeps running out ends FAILED
+// after the failed-attempt retries instead of spending every conflict
+// retry -- and the waits between them.
 __device__ __forceinline__ int out_of_cap(Ctx& c) {
   c.capped = 1;
-  return out_of_cap(c);
+  return c.foreign ? ST_CONFLICT : ST_FAILED;
+}
+
+// No way on: every candidate slot or bin is claimed or already this
+// chain's.  With other insertions' claims among them the key is blocked, a
+// conflict like any other (retried up to max_retries); with none, the
+// serial algorithm's failure.
+__device__ __forceinline__ int dead_end(Ctx& c) {
+  if (c.foreign) return ST_CONFLICT;
+  c.capped = 1;
+  return ST_FAILED;
 }
 
 // Claim both free slots of a ghost pair (Sec. 4), the lower bin first: two
@@ -651,7 +661,7 @@ __device__ int insert_queue(const DevTable& t, Ctx& c) {
         // one is not the serial algorithm's failure
         if (foreign) c.foreign = 1;
         int s = first_from<B>(um, h);
-        if (s < 0) return out_of_cap(c);
+        if (s < 0) return dead_end(c);
         if (c.kicks == t.cap) return out_of_cap(c);
         if (int r0 = plan_room(t, c)) return r0;
         const bool rev = (own >> s) & 1u;
@@ -738,7 +748,7 @@ __device__ inline int insert_random_dary(const DevTable& t, Ctx& c) {
       c.reviews += nc;
       continue;
     }
-    if (nc == 0) return out_of_cap(c);
+    if (nc == 0) return dead_end(c);
     uint32_t k = (uint32_t)(draw(t, c.key, c.draws++, c.attempt) % nc);
     uint32_t x = cb[k];
     View<1> vx = cv[k];

@@ -379,7 +379,7 @@ __device__ int insert_search(const DevTable& t, Ctx& c, uint8_t* region) {
       ry[nr] = y;
       nr++;
     }
-    if (nr == 0) return out_of_cap(c);
+    if (nr == 0) return dead_end(c);
     for (uint32_t i = 0; i < nr; i++) {
       const uint32_t g = rg[i], s = rs[i], y = ry[i];
       View<B> vy;
@@ -551,7 +551,7 @@ __device__ int insert_search_dary(const DevTable& t, Ctx& c, uint8_t* region) {
       ry[nr] = y;
       nr++;
     }
-    if (nr == 0) return out_of_cap(c);
+    if (nr == 0) return dead_end(c);
     for (uint32_t i = 0; i < nr; i++) {
       const uint32_t g = rg[i], y = ry[i];
       View<1> vy;
