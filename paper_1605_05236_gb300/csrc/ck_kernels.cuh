@@ -102,9 +102,12 @@ __device__ __forceinline__ int insert_one(const DevTable& t, Ctx& c, uint8_t* re
       if (c.long_id >= 0 || !grow_plan(t, c)) { st = c.long_id >= 0 ? ST_FAILED : ST_ABORTED; break; }
       continue;
     }
+    // a walk or search that ran out is retried at most six times, or 32
+    // times while it meets other insertions' claims on the way (they
+    // finish meanwhile); then the key is FAILED
     const bool ran_out = st == ST_FAILED || (st == ST_CONFLICT && c.capped);
     if (ran_out) {
-      if (!retry_failed || ++fails > 6) {
+      if (!retry_failed || ++fails > (st == ST_FAILED ? 6u : 32u)) {
         st = ST_FAILED;
         break;
       }

@@ -16,21 +16,24 @@ pytestmark = pytest.mark.gpu
 
 
 def crossed_pairs(bins, n_pairs, seed):
+    """Distinct keys, in pairs whose bins are the same two in opposite
+    order; no key and no bin pair used twice."""
     ref = oracle.OracleTable(bins, 4, 2, oracle.RANDOM, rng_seed=1)
     pool, _ = inputs.distinct_keys(1 << 17, seed)
-    by_bins = {}
-    out = []
-    used = set()
+    first = {}  # (b0, b1) -> the first key seen with those bins
+    out, used_bins = [], set()
     for k in pool:
-        b0, b1 = ref.bins_of(int(k))
-        other = by_bins.get((b1, b0))
-        if other is not None and other not in used and (b0, b1) not in used:
-            out += [other, int(k)]
-            used.add(other)
-            used.add((b0, b1))
+        k = int(k)
+        b0, b1 = ref.bins_of(k)
+        other = first.get((b1, b0))
+        if other is not None and (b0, b1) not in used_bins and (b1, b0) not in used_bins:
+            out += [other, k]
+            used_bins.update({(b0, b1), (b1, b0)})
             if len(out) >= 2 * n_pairs:
                 break
-        by_bins.setdefault((b0, b1), int(k))
+        elif (b0, b1) not in first:
+            first[(b0, b1)] = k
+    assert len(set(out)) == len(out)
     return np.array(out, dtype=np.uint32)
 
 
