@@ -22,9 +22,9 @@
 // to 32 of them.  The owner lane claims the path and its terminal exactly
 // as the per-thread search does (ck_search.cuh) and commits with the same
 // code.  A search that needs more groups than shared memory holds (128),
-// or runs out of budget, is handed to the per-thread
-// search (which retries in a larger space), so every key ends as it would
-// in k_insert.
+// runs out of budget, or finds no way on (with other insertions' claims in
+// its path or not) is handed to the per-thread search, with that search's
+// retries (in a larger space), so every key ends as it would in k_insert.
 #pragma once
 #include "ck_kernels.cuh"
 
