@@ -166,15 +166,14 @@ __device__ __forceinline__ uint32_t pick(const uint32_t (&a)[N], uint32_t s) {
   return r;
 }
 
-// The group a search spawns from: its records' next bins and which of them
-// may spawn, taken when the search starts popping the group (again after it
-// popped another).  A two-choice group's bin is read with one vector load
-// and each record's other bin probed in the visited set, the probes
-// overlapping; a d-ary group's record gives its d bins.  `ok` bit s: record
-// s is present and its bin y[s] was unvisited at that point.  Until the
-// search pops another group, the only bins it marks visited are those its
-// spawns from this group view (`spawned`), so ok and spawned together give
-// exactly the visited test the search makes spawn by spawn.
+// The group a d-ary BFS spawns from: its record's d bins (y[j]: the bin of
+// hash function j) and which of them may be tried, taken when the search
+// reaches the group, the visited-set probes of the d bins overlapping.  `ok`
+// bit j: the record is present, y[j] is not its own bin, and y[j] was
+// unvisited then.  Until the search moves on to the next group, the only
+// bins it marks visited are those its tries from this group view
+// (`spawned`), so ok and spawned together give exactly the visited test the
+// search makes try by try.
 template <int N>
 struct GroupCache {
   uint32_t g;  // group index (~0u: none yet)
